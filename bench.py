@@ -1,0 +1,373 @@
+"""Benchmark of the xorgens GPU path (one JSON line on stdout).
+
+Step = one pass of the generation hot path over the many-streams workload:
+16384 streams (seeds 1..16384), 2^16 u32 words per stream (2^30 words, 4 GiB)
+then 2^16 FP32 uniforms per stream (another 4 GiB), with the stream state
+resident in HBM and advancing from step to step.  value = RN/s over the timed
+steps (CUDA events on the launching stream, max over ranks).  The outputs
+(8 GiB per step) are far larger than L2 (129 MB), so no flush is needed.
+
+Beside the headline it reports the same metric end to end through the C ABI
+into pinned host memory (e2e), the roofline of the dominant kernel against
+the measured HBM peak, per-row figures (normals, fused sum), the SM clocks
+seen during the timed region, and the CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1108_0486_gb300 import workloads as W  # noqa: E402
+
+STREAMS = W.MANY_STREAMS["streams"]
+N_PER = W.MANY_STREAMS["n"]
+WORKLOAD = ("16384 streams (seeds 1..16384), 2^16 u32 + 2^16 FP32 uniforms per stream "
+            "per step (2^31 RNs, 8 GiB written); xorgens (r,s,a,b,c,d)=(128,95,17,12,13,15), Weyl on")
+CONFIG = {"workload": WORKLOAD, "streams": STREAMS, "n_per_stream": N_PER,
+          "outputs": ["u32", "uniform_f32"], "param_set": "(128,95,17,12,13,15)",
+          "l2_flush": "none needed: 8 GiB of outputs per step >> 129 MB L2"}
+METRIC, UNIT = "RN/s", "RN/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- oracle
+
+def cpu_baseline(target_s: float = 10.0):
+    """The CPU oracle as it stands, threaded over streams on every host core
+    (ctypes releases the GIL), on a sample of the workload's streams."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    O.lib()
+
+    def run(seed_list):
+        threads = []
+        parts = np.array_split(seed_list, cores)
+        for p in parts:
+            if p.size == 0:
+                continue
+            def job(p=p):
+                O.streams(p, N_PER, kind="u32")
+                O.streams(p, N_PER, kind="uniform")
+            threads.append(threading.Thread(target=job))
+        t0 = time.perf_counter()
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        return time.perf_counter() - t0
+
+    probe = W.seeds(cores * 2)
+    dt = run(probe)
+    per_stream = dt / probe.size
+    n_streams = int(min(STREAMS, max(cores, target_s / max(per_stream, 1e-9))))
+    sample = W.seeds(n_streams)
+    dt = run(sample)
+    rns = n_streams * 2 * N_PER / dt
+    return {"value": rns, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_streams} of the 16384 streams, 2^16 u32 + 2^16 uniforms each "
+                      f"({n_streams * 2 * N_PER} RNs, {dt:.1f} s wall on {cores} threads)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    O.lib()
+    cores = os.cpu_count() or 1
+    base = cpu_baseline(target_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+    n_streams = int(base["sample"].split(" of ")[0])
+    sample = W.seeds(n_streams)
+
+    def step():
+        parts = np.array_split(sample, cores)
+        th = []
+        for p in parts:
+            if p.size:
+                th.append(threading.Thread(target=lambda p=p: (O.streams(p, N_PER, kind="u32"),
+                                                               O.streams(p, N_PER, kind="uniform"))))
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    rns = n_streams * 2 * N_PER * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": rns, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": rns, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {n_streams} of the 16384 streams, "
+                                       "2^16 u32 + 2^16 uniforms each"},
+            "e2e": {"value": rns, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1108_0486_gb300 import Streams, _lib as L
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    # weak scaling: every rank owns its own 16384 streams (seeds offset by rank)
+    seeds = W.seeds(STREAMS, start=1 + rank * STREAMS)
+    st = Streams(STREAMS, seeds=seeds, stream=stream)
+    buf_u = torch.empty((STREAMS, N_PER), dtype=torch.int32, device="cuda")
+    buf_f = torch.empty((STREAMS, N_PER), dtype=torch.float32, device="cuda")
+    launches_per_step = 2
+
+    ev = []  # (start, mid, end) events per step: u32 kernel, uniform kernel
+
+    def step(record=False):
+        if record:
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            st.u32(N_PER, out=buf_u)
+            e1.record(stream)
+            st.uniform(N_PER, out=buf_f)
+            e2.record(stream)
+            ev.append((e0, e1, e2))
+        else:
+            st.u32(N_PER, out=buf_u)
+            st.uniform(N_PER, out=buf_f)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    ms = t_start.elapsed_time(t_end)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_u = [a.elapsed_time(b) for a, b, _ in ev]
+    ms_f = [b.elapsed_time(c) for _, b, c in ev]
+    rns_per_step = STREAMS * N_PER * 2
+    value = rns_per_step * args.steps * ws / (ms / 1e3)
+    peak, peak_kind = _peaks()
+    bytes_per_launch = STREAMS * N_PER * 4
+    avg_u = sum(ms_u) / len(ms_u)
+    avg_f = sum(ms_f) / len(ms_f)
+    dom_ms, dom_name = (avg_u, "gen_kernel<u32>") if avg_u >= avg_f else (avg_f, "gen_kernel<uniform>")
+    achieved = bytes_per_launch / (dom_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": args.traffic,
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "per_kernel_ms": {"u32": avg_u, "uniform": avg_f}}
+
+    rows = {}
+    if not args.quick:
+        rows = extra_rows(st, stream, torch, peak)
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(st, stream, torch, L, args)
+    torch.cuda.synchronize()
+    st.close()
+    del buf_u, buf_f
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": dict(CONFIG, parallelism=f"independent streams x{ws}"),
+                "roofline": roofline, "gpu_launches": launches_per_step * args.steps,
+                "clocks": clk, "e2e": e2e, "rows": rows}
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _time(fn, stream, torch, reps=5, warm=2):
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return sum(ts) / len(ts)
+
+
+def extra_rows(st, stream, torch, peak):
+    """Other rows of the path on the same streams: normals (2^30 FP32 over
+    16384 streams) and the fused normal sum (no bulk HBM write)."""
+    rows = {}
+    n = W.NORMALS["n"]
+    buf = torch.empty((STREAMS, n), dtype=torch.float32, device="cuda")
+    ms = _time(lambda: st.normal(n, out=buf), stream, torch)
+    rn = STREAMS * n
+    rows["normal"] = {"rn_s": rn / (ms / 1e3), "ms": ms,
+                      "hbm_frac": rn * 4 / (ms / 1e3) / 1e9 / peak, "launch": st.get_launch("normal")}
+    sums = torch.empty(STREAMS, dtype=torch.float32, device="cuda")
+    ms = _time(lambda: st.normal_sum(n, out=sums), stream, torch)
+    rows["normal_sum_fused"] = {"rn_s": rn / (ms / 1e3), "ms": ms, "hbm_bytes_written": STREAMS * 4}
+    ms = _time(lambda: st.u32(n, out=buf.view(torch.int32)), stream, torch)
+    rows["u32"] = {"rn_s": rn / (ms / 1e3), "ms": ms, "hbm_frac": rn * 4 / (ms / 1e3) / 1e9 / peak}
+    del buf
+    return rows
+
+
+def end_to_end(st, stream, torch, L, args):
+    """The same step through the C ABI into pinned host memory: each call
+    generates on the device in pieces and copies them to the host while the
+    next piece is generated; the timed region includes every copy."""
+    host = torch.empty((STREAMS, N_PER), dtype=torch.int32, pin_memory=True)
+    hostf = torch.empty((STREAMS, N_PER), dtype=torch.float32, pin_memory=True)
+    ptr_u, ptr_f = host.data_ptr(), hostf.data_ptr()
+
+    def step():
+        L.xg_generate_u32(st.ctx, 0, STREAMS, N_PER, ptr_u, N_PER)
+        L.xg_generate_uniform(st.ctx, 0, STREAMS, N_PER, ptr_f, N_PER)
+
+    step()
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rns = STREAMS * N_PER * 2 * k / dt
+    return {"value": rns, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": STREAMS * N_PER * 8, "steps": k,
+            "note": "host buffers are pinned; no inputs cross per step (state resident)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the extra rows")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel, if measured")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,158 @@
+/*
+ * xorgens_gb300 -- C ABI of a GB300 (sm_103a) library of xorgens generators.
+ *
+ * The generator is the one of Nandapalan, Brent, Murray and Rendell,
+ * "High-Performance Pseudo-Random Number Generation on Graphics Processing
+ * Units" (arXiv:1108.0486):
+ *   x_k = x_{k-r}(I + L^a)(I + R^b) xor x_{k-s}(I + L^c)(I + R^d)   (Sec. 2)
+ *   w_k = w_{k-1} + omega mod 2^32                                   (Sec. 1.5)
+ *   out_k = x_k + (w_k xor (w_k >> 16)) mod 2^32                     (Eq. 1)
+ * with 32-bit words, r = 128 and one of two compile-time parameter sets:
+ *   XG_PARAMS_DEFAULT  (r,s,a,b,c,d) = (128, 95, 17, 12, 13, 15)
+ *   XG_PARAMS_PAPER    (r,s,a,b,c,d) = (128, 65, 15, 14, 12, 17)  (Sec. 2)
+ * Each stream is one generator: r state words plus a Weyl word plus a
+ * position (Sec. 2: "a small constant for the Weyl generator and a circular
+ * array index").  Many independent streams live in one context, resident in
+ * device memory (Sec. 2, independent subsequences; Sec. 4, one seed per
+ * block id).
+ *
+ * Conventions for every entry point:
+ *   - Returns an xg_status; never throws or aborts.  On failure the
+ *     thread-local message of xg_last_error() says why.
+ *   - Device pointers are CUDA device memory of the current device (for
+ *     example a torch tensor's data pointer); host pointers are ordinary
+ *     (pageable or pinned) host memory.  The library never frees caller memory.
+ *   - Work is enqueued on the context's CUDA stream and is asynchronous unless
+ *     the entry point says otherwise.  Calls on one context must come from one
+ *     host thread at a time.
+ *   - Stream positions advance with every call, in call order.  Any split of
+ *     a stream's output into consecutive calls concatenates to the same
+ *     sequence as one call, for every output type and launch configuration.
+ */
+#ifndef XORGENS_GB300_H
+#define XORGENS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xg_ctx xg_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    XG_OK = 0,
+    XG_EINVAL = 1,     /* bad argument: null pointer, range, alignment, size */
+    XG_ENOMEM = 2,     /* device or host allocation failed */
+    XG_EAGAIN = 3,     /* admission refused: the output memory cap is reached */
+    XG_ETIMEDOUT = 4,  /* a bounded wait gave up */
+    XG_ECUDA = 5,      /* a CUDA runtime call failed (message has the CUDA error) */
+    XG_ENOTFOUND = 6,  /* unknown ticket */
+    XG_EDEVICE = 7     /* a kernel reported an internal error through its status word */
+} xg_status;
+
+typedef enum {
+    XG_U32 = 0,         /* the output word itself, Eq. (1) */
+    XG_UNIFORM_F32 = 1, /* (out >> 8) * 2^-24, exact, in [0, 1) */
+    XG_NORMAL_F32 = 2   /* Box-Muller on consecutive word pairs (o1, o2):
+                           u1 = ((o1 >> 8) + 1) 2^-24, u2 = (o2 >> 8) 2^-24,
+                           z1 = sqrt(-2 ln u1) cos(2 pi u2),
+                           z2 = sqrt(-2 ln u1) sin(2 pi u2).
+                           n normals consume 2*ceil(n/2) words; pairs start at
+                           the call's first word; when n is odd the last z2 is
+                           dropped.  Within 4 ulp of the exact value. */
+} xg_type;
+
+enum { XG_PARAMS_DEFAULT = 0, XG_PARAMS_PAPER = 1 };
+
+/* ---- contexts and state ------------------------------------------------- */
+
+/* Create n_streams generators (all unseeded: call xg_seed before use).
+ * param_set: XG_PARAMS_DEFAULT or XG_PARAMS_PAPER.  weyl_on: 1 for Eq. (1),
+ * 0 to output the GF(2)-linear part x_k alone (for testing).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream) owned by the caller; it must
+ * outlive the context.  Allocates the device state: 776 bytes per stream. */
+xg_status xg_create_streams(xg_ctx** out, uint32_t n_streams, uint32_t param_set,
+                            uint32_t weyl_on, void* cuda_stream);
+
+/* Wait for the context's work, stop its server if running, free everything. */
+xg_status xg_destroy(xg_ctx* ctx);
+
+/* Change the CUDA stream later calls enqueue on (cudaStream_t). */
+xg_status xg_set_stream(xg_ctx* ctx, void* cuda_stream);
+
+/* Number of streams in the context. */
+xg_status xg_num_streams(const xg_ctx* ctx, uint32_t* n_streams);
+
+/* Seed streams [first, first+count) from host_seeds[0..count): expands each
+ * 32-bit seed into r = 128 state words and a Weyl word with Marsaglia's
+ * 64-bit xorshift (shift triple 13, 7, 17), then runs the generator for
+ * 4r = 512 words and discards them (the paper defers seeding to the xorgens
+ * package, Sec. 1.5 and Sec. 4; this is the library's own procedure).
+ * Consecutive seeds (block ids, Sec. 4) give unrelated streams. */
+xg_status xg_seed(xg_ctx* ctx, uint32_t first, uint32_t count, const uint32_t* host_seeds);
+
+/* Checkpoint: the stream's r = 128 most recent state words, oldest first,
+ * and its Weyl word, into host memory.  Synchronises the context's stream. */
+xg_status xg_get_state(xg_ctx* ctx, uint32_t stream, uint32_t* host_ring128,
+                       uint32_t* host_weyl);
+
+/* Restore a state written by xg_get_state (or any nonzero state).  After it
+ * the stream continues exactly as the checkpointed one did.  Synchronous. */
+xg_status xg_set_state(xg_ctx* ctx, uint32_t stream, const uint32_t* host_ring128,
+                       uint32_t weyl);
+
+/* ---- plain generation (one kernel launch per call) --------------------- */
+
+/* Write n_per_stream outputs of each stream in [first, first+nstreams) to
+ * out + (i - first) * ld (elements), stream-major.  ld >= n_per_stream.
+ * out may be device memory (asynchronous on the context's stream) or host
+ * memory (the library generates into its own device buffer in chunks and
+ * copies them to the host, overlapping both; returns when the data is there).
+ * The fast path needs out and ld*4 bytes 16-byte aligned; other alignments
+ * are accepted and use scalar stores. */
+xg_status xg_generate_u32(xg_ctx* ctx, uint32_t first, uint32_t nstreams,
+                          uint64_t n_per_stream, uint32_t* out, uint64_t ld);
+xg_status xg_generate_uniform(xg_ctx* ctx, uint32_t first, uint32_t nstreams,
+                              uint64_t n_per_stream, float* out, uint64_t ld);
+xg_status xg_generate_normal(xg_ctx* ctx, uint32_t first, uint32_t nstreams,
+                             uint64_t n_per_stream, float* out, uint64_t ld);
+
+/* Fused mode: generate n_per_stream normals per stream exactly as
+ * xg_generate_normal would (the streams advance the same way) but write only
+ * their FP32 sum per stream to d_sums[i - first] (device memory).  The sum
+ * order is fixed by the launch configuration (xg_get_launch): each lane adds
+ * its own values in sequence order, then the lanes of a stream are combined
+ * by a butterfly over lane offsets TPG/2, ..., 1. */
+xg_status xg_generate_normal_sum(xg_ctx* ctx, uint32_t first, uint32_t nstreams,
+                                 uint64_t n_per_stream, float* d_sums);
+
+/* Conversions alone: apply the XG_UNIFORM_F32 / XG_NORMAL_F32 transform to
+ * n words already in device memory (d_words), writing n floats to d_out.
+ * For the normal transform, n must be even (pairs (d_words[2i],
+ * d_words[2i+1])). */
+xg_status xg_transform_uniform(xg_ctx* ctx, const uint32_t* d_words, uint64_t n, float* d_out);
+xg_status xg_transform_normal(xg_ctx* ctx, const uint32_t* d_words, uint64_t n, float* d_out);
+
+/* ---- launch configuration --------------------------------------------- */
+
+/* Threads per generator (tpg) and words per thread per round (wpl) used for
+ * an output type; tpg*wpl is the round width (32 or 64 words, never more than
+ * s, so that every word of a round depends only on earlier rounds, Sec. 2).
+ * Supported pairs: (4,8) (8,4) (16,2) (16,4) (32,2).  0,0 = autotune. */
+xg_status xg_set_launch(xg_ctx* ctx, xg_type type, uint32_t tpg, uint32_t wpl);
+xg_status xg_get_launch(const xg_ctx* ctx, xg_type type, uint32_t* tpg, uint32_t* wpl);
+
+/* ---- errors ------------------------------------------------------------- */
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* xg_last_error(void);
+
+/* Library version string. */
+const char* xg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XORGENS_GB300_H */

@@ -96,6 +96,7 @@ def lib():
             L.xgo_seed32.argtypes = [G, u32]; L.xgo_seed32.restype = ctypes.c_int
             L.xgo_uniform.argtypes = [u32]; L.xgo_uniform.restype = ctypes.c_float
             L.xgo_normal_pair.argtypes = [u32, u32, p, p]
+            L.xgo_normal_pairs.argtypes = [p, u64, p]
             for f in ("xgo_fill_u32", "xgo_fill_raw", "xgo_fill_uniform", "xgo_fill_normal"):
                 getattr(L, f).argtypes = [G, u64, p]
             L.xgo_sum_normal.argtypes = [G, u64]; L.xgo_sum_normal.restype = ctypes.c_double
@@ -207,6 +208,15 @@ def normal_pair64(o1: int, o2: int):
     z1 = np.zeros(1); z2 = np.zeros(1)
     lib().xgo_normal_pair(o1 & 0xFFFFFFFF, o2 & 0xFFFFFFFF, _ptr(z1), _ptr(z2))
     return float(z1[0]), float(z2[0])
+
+
+def normal_pairs64(words) -> np.ndarray:
+    """FP64 Box-Muller of consecutive word pairs (2i, 2i+1)."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).ravel())
+    assert w.size % 2 == 0
+    out = np.empty(w.size, dtype=np.float64)
+    lib().xgo_normal_pairs(_ptr(w), w.size // 2, _ptr(out))
+    return out
 
 
 def streams(seeds, n: int, kind: str = "u32", param_set: int = 0, weyl=True) -> np.ndarray:

@@ -22,10 +22,10 @@
  *     to w/2.  (I + R^gamma) maps w to w xor (w >> gamma); "+ mod 2^w" is
  *     integer addition.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   omega = the odd integer nearest 2^{w-1}(sqrt 5 - 1)  (0x9E3779B9 at w=32),
  *   gamma = w/2, the Weyl word is advanced before use, seeding is this
- *   project's own definition (xg_oracle_seed32 below; the paper defers to the
+ *   project's own definition (xgo_seed32 below; the paper defers to the
  *   xorgens package, which is not available -- parity unpinned), and the
  *   uniform / normal conversions are this project's definitions (the paper
  *   has none): uniform = (out >> 8) * 2^-24, normal = Box-Muller in FP64.
@@ -281,3 +281,10 @@ uint64_t xgo_cycle_length(const xgo_gen* g0, uint64_t limit)
 }
 
 size_t xgo_sizeof(void) { return sizeof(xgo_gen); }
+
+/* xgo_normal_pair over n_pairs given word pairs (words[2i], words[2i+1]). */
+void xgo_normal_pairs(const uint32_t* words, uint64_t n_pairs, double* out)
+{
+    for (uint64_t i = 0; i < n_pairs; ++i)
+        xgo_normal_pair(words[2 * i], words[2 * i + 1], &out[2 * i], &out[2 * i + 1]);
+}

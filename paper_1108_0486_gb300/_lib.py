@@ -1,0 +1,161 @@
+"""ctypes binding of the C ABI in include/xorgens_gb300.h.
+
+Argument marshalling only: every function here forwards to the entry point
+of the same name in the in-tree shared library and raises XGError when it
+returns a nonzero status.  Loading fails loudly when the library has not been
+built; nothing here computes random numbers itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB_PATH
+
+XG_OK, XG_EINVAL, XG_ENOMEM, XG_EAGAIN, XG_ETIMEDOUT, XG_ECUDA, XG_ENOTFOUND, XG_EDEVICE = range(8)
+XG_U32, XG_UNIFORM_F32, XG_NORMAL_F32 = 0, 1, 2
+STATUS_NAMES = {0: "XG_OK", 1: "XG_EINVAL", 2: "XG_ENOMEM", 3: "XG_EAGAIN", 4: "XG_ETIMEDOUT",
+                5: "XG_ECUDA", 6: "XG_ENOTFOUND", 7: "XG_EDEVICE"}
+
+
+class XGError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+u32, u64, vp, i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+P_u32, P_u64, P_vp, P_i32 = (ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
+                             ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int))
+
+# name -> argtypes (all return xg_status unless listed in _RESTYPES)
+SIGNATURES = {
+    "xg_create_streams": [P_vp, u32, u32, u32, vp],
+    "xg_destroy": [vp],
+    "xg_set_stream": [vp, vp],
+    "xg_num_streams": [vp, P_u32],
+    "xg_seed": [vp, u32, u32, vp],
+    "xg_get_state": [vp, u32, vp, P_u32],
+    "xg_set_state": [vp, u32, vp, u32],
+    "xg_generate_u32": [vp, u32, u32, u64, vp, u64],
+    "xg_generate_uniform": [vp, u32, u32, u64, vp, u64],
+    "xg_generate_normal": [vp, u32, u32, u64, vp, u64],
+    "xg_generate_normal_sum": [vp, u32, u32, u64, vp],
+    "xg_transform_uniform": [vp, vp, u64, vp],
+    "xg_transform_normal": [vp, vp, u64, vp],
+    "xg_set_launch": [vp, i32, u32, u32],
+    "xg_get_launch": [vp, i32, P_u32, P_u32],
+    "xg_last_error": [],
+    "xg_version": [],
+}
+_RESTYPES = {"xg_last_error": ctypes.c_char_p, "xg_version": ctypes.c_char_p}
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = _RESTYPES.get(name, ctypes.c_int)
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().xg_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != XG_OK:
+        raise XGError(status, last_error())
+
+
+def call(name: str, *args) -> None:
+    check(getattr(lib(), name)(*args))
+
+
+# ---- functions with the C names (argument marshalling only) -------------
+
+def xg_create_streams(n_streams: int, param_set: int = 0, weyl_on: bool = True,
+                      cuda_stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    call("xg_create_streams", ctypes.byref(h), n_streams, param_set, int(bool(weyl_on)),
+         ctypes.c_void_p(cuda_stream))
+    return h.value
+
+
+def xg_destroy(ctx: int) -> None:
+    call("xg_destroy", ctypes.c_void_p(ctx))
+
+
+def xg_set_stream(ctx: int, cuda_stream: int) -> None:
+    call("xg_set_stream", ctypes.c_void_p(ctx), ctypes.c_void_p(cuda_stream))
+
+
+def xg_num_streams(ctx: int) -> int:
+    n = ctypes.c_uint32()
+    call("xg_num_streams", ctypes.c_void_p(ctx), ctypes.byref(n))
+    return n.value
+
+
+def xg_seed(ctx: int, first: int, count: int, host_seeds_ptr: int) -> None:
+    call("xg_seed", ctypes.c_void_p(ctx), first, count, ctypes.c_void_p(host_seeds_ptr))
+
+
+def xg_get_state(ctx: int, stream: int, host_ring_ptr: int) -> int:
+    w = ctypes.c_uint32()
+    call("xg_get_state", ctypes.c_void_p(ctx), stream, ctypes.c_void_p(host_ring_ptr), ctypes.byref(w))
+    return w.value
+
+
+def xg_set_state(ctx: int, stream: int, host_ring_ptr: int, weyl: int) -> None:
+    call("xg_set_state", ctypes.c_void_p(ctx), stream, ctypes.c_void_p(host_ring_ptr), weyl & 0xFFFFFFFF)
+
+
+def xg_generate_u32(ctx, first, nstreams, n_per_stream, out_ptr, ld) -> None:
+    call("xg_generate_u32", ctypes.c_void_p(ctx), first, nstreams, n_per_stream, ctypes.c_void_p(out_ptr), ld)
+
+
+def xg_generate_uniform(ctx, first, nstreams, n_per_stream, out_ptr, ld) -> None:
+    call("xg_generate_uniform", ctypes.c_void_p(ctx), first, nstreams, n_per_stream, ctypes.c_void_p(out_ptr), ld)
+
+
+def xg_generate_normal(ctx, first, nstreams, n_per_stream, out_ptr, ld) -> None:
+    call("xg_generate_normal", ctypes.c_void_p(ctx), first, nstreams, n_per_stream, ctypes.c_void_p(out_ptr), ld)
+
+
+def xg_generate_normal_sum(ctx, first, nstreams, n_per_stream, sums_ptr) -> None:
+    call("xg_generate_normal_sum", ctypes.c_void_p(ctx), first, nstreams, n_per_stream, ctypes.c_void_p(sums_ptr))
+
+
+def xg_transform_uniform(ctx, words_ptr, n, out_ptr) -> None:
+    call("xg_transform_uniform", ctypes.c_void_p(ctx), ctypes.c_void_p(words_ptr), n, ctypes.c_void_p(out_ptr))
+
+
+def xg_transform_normal(ctx, words_ptr, n, out_ptr) -> None:
+    call("xg_transform_normal", ctypes.c_void_p(ctx), ctypes.c_void_p(words_ptr), n, ctypes.c_void_p(out_ptr))
+
+
+def xg_set_launch(ctx, out_type, tpg, wpl) -> None:
+    call("xg_set_launch", ctypes.c_void_p(ctx), out_type, tpg, wpl)
+
+
+def xg_get_launch(ctx, out_type):
+    t, w = ctypes.c_uint32(), ctypes.c_uint32()
+    call("xg_get_launch", ctypes.c_void_p(ctx), out_type, ctypes.byref(t), ctypes.byref(w))
+    return t.value, w.value
+
+
+def xg_version() -> str:
+    return lib().xg_version().decode()

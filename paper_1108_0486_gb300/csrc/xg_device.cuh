@@ -1,0 +1,196 @@
+// Device-side building blocks of the xorgens kernels (sm_103a).
+//
+// The generator (arXiv:1108.0486):
+//   Sec. 2    x_k = x_{k-r}(I+L^a)(I+R^b) xor x_{k-s}(I+L^c)(I+R^d), r = 128 words
+//   Sec. 1.5  w_k = w_{k-1} + omega,  out_k = x_k + (w_k xor (w_k >> gamma))  (Eq. 1)
+//
+// Parallel structure (Sec. 2, dependency analysis): x_k reads only x_{k-s} and
+// x_{k-r}, so the words x_k .. x_{k+s-1} depend only on words before x_k.  A
+// "round" here computes RW = 32 or 64 consecutive words at once (RW <= s for
+// both parameter sets): a group of TPG lanes of one warp, each lane owning WPL
+// consecutive words of the round (TPG * WPL = RW).  The 128-word ring lives in
+// registers as NROWS = 128 / RW rows of WPL words per lane; lane j of row t
+// holds ring words RW*t + WPL*j .. RW*t + WPL*j + WPL-1 (row 0 = oldest).  The
+// lag-r input of a word sits in the same lane and element of row 0; the lag-s
+// input is at ring position (128 - s) + q, which is in the same lane for all
+// but one element per lane per round, fetched with one warp shuffle.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "xg_launch.h"
+
+namespace xg {
+
+// Weyl increment: the odd integer nearest 2^31 (sqrt(5) - 1) (Sec. 1.5).
+constexpr uint32_t kOmega = 0x9E3779B9u;
+// Output shift gamma = w / 2 (Sec. 1.5, Eq. 1).
+constexpr int kGamma = 16;
+// Degree r = ring words, the same for both parameter sets.
+constexpr int kR = 128;
+
+template <int S_, int A_, int B_, int C_, int D_>
+struct Params {
+    static constexpr int R = kR, S = S_, A = A_, B = B_, C = C_, D = D_;
+};
+// (r,s,a,b,c,d) = (128,95,17,12,13,15): the library's default set.
+using ParamsDefault = Params<95, 17, 12, 13, 15>;
+// (r,s,a,b,c,d) = (128,65,15,14,12,17): the set of the paper's results (Sec. 2).
+using ParamsPaper = Params<65, 15, 14, 12, 17>;
+
+// Eq. (1): w (I + R^gamma) + x mod 2^32.
+__device__ __forceinline__ uint32_t combine(uint32_t x, uint32_t w)
+{
+    return x + (w ^ (w >> kGamma));
+}
+
+// Uniform in [0,1): (out >> 8) * 2^-24; exact in binary32.
+__device__ __forceinline__ float to_uniform(uint32_t o)
+{
+    return __fmul_rn(__uint2float_rn(o >> 8), 0x1p-24f);
+}
+
+// ---------------------------------------------------------------------------
+// Box-Muller in binary32.  Coefficients: derive_normal_coeffs.py (Remez
+// minimax fits; relative errors Q 4.1e-9, S 3.2e-9, C 6.4e-11).
+//   ln(1+t)       = t + t^2 Q(t),   t in [sqrt(1/2)-1, sqrt(2)-1]
+//   sin(pi x / 4) = x S(x^2),       x in [-1, 1]
+//   cos(pi x / 4) = 1 + x^2 C(x^2)
+__device__ constexpr float kLogQ[9] = {-0x1.fffff8p-2f, 0x1.55555p-2f,   -0x1.000426p-2f,
+                            0x1.99a3f2p-3f,  -0x1.54276ep-3f, 0x1.22719cp-3f,
+                            -0x1.0f3766p-3f, 0x1.084866p-3f,  -0x1.383026p-4f};
+__device__ constexpr float kSinS[4] = {0x1.921fb6p-1f, -0x1.4abbbap-4f, 0x1.465e92p-9f, -0x1.2d9302p-15f};
+// pi/4 - kSinS[0], so that x * pi/4 is formed with a single rounding.
+constexpr float kSinS0Lo = -0x1.777a5cp-26f;
+__device__ constexpr float kCosC[4] = {-0x1.3bd3ccp-2f, 0x1.03c1dep-6f, -0x1.55c5ep-12f, 0x1.d9d57ep-19f};
+// -2 ln 2 = kNeg2Ln2Hi + kNeg2Ln2Lo, with e * kNeg2Ln2Hi exact for |e| <= 24.
+constexpr float kNeg2Ln2Hi = -0x1.62e4p+0f;
+constexpr float kNeg2Ln2Lo = -0x1.7f7d1cp-19f;
+
+// R^2 = -2 ln(m1 2^-24) for m1 in [63, 2^24].
+__device__ __forceinline__ float neg2ln_u1(uint32_t m1)
+{
+    const float fm = __uint2float_rn(m1);                  // exact (m1 <= 2^24)
+    const int bits = __float_as_int(fm);
+    const int k = (bits - 0x3F3504F3) >> 23;               // fm = 2^k f, f in [sqrt(.5), sqrt(2))
+    const float f = __int_as_float(bits - (k << 23));
+    const float t = __fsub_rn(f, 1.0f);                    // exact
+    float q = kLogQ[8];
+#pragma unroll
+    for (int i = 7; i >= 0; --i) q = __fmaf_rn(q, t, kLogQ[i]);
+    const float lnf = __fmaf_rn(__fmul_rn(t, t), q, t);    // ln f
+    const float e = __int2float_rn(k - 24);                // u1 = 2^e f
+    return __fmaf_rn(e, kNeg2Ln2Hi, __fmaf_rn(e, kNeg2Ln2Lo, __fmul_rn(-2.0f, lnf)));
+}
+
+// sqrt(L) with one Newton correction of the hardware reciprocal square root.
+__device__ __forceinline__ float sqrt_refined(float L)
+{
+    const float y = rsqrtf(fmaxf(L, 0x1p-100f));
+    const float r0 = __fmul_rn(L, y);
+    const float d = __fmaf_rn(-r0, r0, L);
+    return __fmaf_rn(d, __fmul_rn(0.5f, y), r0);
+}
+
+// Tail branch (R > 5, i.e. m1 <= 62, probability 62 * 2^-24 per pair): FP64.
+static __device__ __noinline__ void normal_pair_fp64(uint32_t m1, uint32_t m2, float& z1, float& z2)
+{
+    const double u1 = (double)m1 * 0x1p-24;
+    const double R = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi((double)m2 * 0x1p-23, &s, &c);
+    z1 = (float)(R * c);
+    z2 = (float)(R * s);
+}
+
+__device__ __forceinline__ void normal_pair(uint32_t o1, uint32_t o2, float& z1, float& z2)
+{
+    const uint32_t m1 = (o1 >> 8) + 1u;   // u1 = m1 2^-24 in (0, 1]
+    const uint32_t m2 = o2 >> 8;          // u2 = m2 2^-24 in [0, 1)
+    if (m1 <= 62u) {
+        normal_pair_fp64(m1, m2, z1, z2);
+        return;
+    }
+    const float R = sqrt_refined(neg2ln_u1(m1));
+    // angle 2 pi u2 = n (pi/2) + (pi/4) x, reduced exactly in integers
+    const uint32_t q = (m2 + (1u << 21)) >> 22;                  // 0..4
+    const int rr = (int)m2 - (int)(q << 22);                     // [-2^21, 2^21)
+    const float x = __fmul_rn(__int2float_rn(rr), 0x1p-21f);     // exact
+    const float y = __fmul_rn(x, x);
+    const float ylo = __fmaf_rn(x, x, -y);                       // x^2 = y + ylo exactly
+    float sp = kSinS[3];
+    sp = __fmaf_rn(sp, y, kSinS[2]);
+    sp = __fmaf_rn(sp, y, kSinS[1]);
+    const float s = __fmaf_rn(x, kSinS[0], __fmaf_rn(x, kSinS0Lo, __fmul_rn(__fmul_rn(x, y), sp)));
+    float cp = kCosC[3];
+    cp = __fmaf_rn(cp, y, kCosC[2]);
+    cp = __fmaf_rn(cp, y, kCosC[1]);
+    cp = __fmaf_rn(cp, y, kCosC[0]);
+    const float c = __fmaf_rn(cp, y, __fmaf_rn(cp, ylo, 1.0f));
+    // quadrant n = q mod 4: (cos, sin) = (c,s), (-s,c), (-c,-s), (s,-c)
+    const uint32_t n = q & 3u;
+    const float cs = (n & 1u) ? s : c;
+    const float sn = (n & 1u) ? c : s;
+    const uint32_t cflip = ((n + 1u) & 2u) << 30;
+    const uint32_t sflip = (n & 2u) << 30;
+    z1 = __fmul_rn(R, __uint_as_float(__float_as_uint(cs) ^ cflip));
+    z2 = __fmul_rn(R, __uint_as_float(__float_as_uint(sn) ^ sflip));
+}
+
+// ---------------------------------------------------------------------------
+// The round engine of one generator group.
+template <class P, int TPG, int WPL>
+struct Engine {
+    static constexpr int WPL_ = WPL;          // words per lane per round
+    static constexpr int TPG_ = TPG;          // lanes per generator
+    static constexpr int RW = TPG * WPL;      // words per round
+    static constexpr int NROWS = kR / RW;     // ring rows held per lane
+    static_assert(RW == 32 || RW == 64, "round width must be 32 or 64 words");
+    static_assert(RW <= P::S, "a round must not read its own words (Sec. 2)");
+    static_assert(TPG >= 1 && TPG <= 32 && (32 % TPG) == 0, "groups tile a warp");
+    // lag-s input of round word q sits at ring position DL + q
+    static constexpr int DL = kR - P::S;
+    static constexpr int ROWD = DL / RW, OFFD = DL % RW;
+    static constexpr int LO = OFFD / WPL, EL = OFFD % WPL;
+
+    uint32_t ring[NROWS][WPL];
+    int lane;        // lane index inside the group, 0..TPG-1
+    unsigned mask;   // the group's lanes in the warp (shuffle mask)
+
+    // One round.  K is the physical row of logical row 0 (the oldest); the new
+    // words overwrite it, so logical row 0 of the next round is row K+1.
+    template <int K>
+    __device__ __forceinline__ void round()
+    {
+        uint32_t v[WPL];
+#pragma unroll
+        for (int i = 0; i < WPL; ++i) {
+            const int el = (i + EL) % WPL;
+            const int delta = LO + (i + EL) / WPL;       // lane offset, 0..TPG
+            const int row = ROWD + delta / TPG;          // logical row
+            const int dl = delta % TPG;
+            if (dl == 0) {
+                v[i] = ring[(K + row) % NROWS][el];
+            } else {
+                // receivers j with j + dl >= TPG read the next row: the
+                // sender L = j + dl - TPG < dl sends that row's word instead
+                const uint32_t send = (lane < dl) ? ring[(K + row + 1) % NROWS][el]
+                                                  : ring[(K + row) % NROWS][el];
+                v[i] = __shfl_sync(mask, send, lane + dl, TPG);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < WPL; ++i) {
+            uint32_t t = ring[K][i];
+            t ^= t << P::A;
+            t ^= t >> P::B;
+            uint32_t u = v[i];
+            u ^= u << P::C;
+            u ^= u >> P::D;
+            ring[K][i] = t ^ u;
+        }
+    }
+};
+
+}  // namespace xg

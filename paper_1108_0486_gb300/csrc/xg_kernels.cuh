@@ -1,0 +1,397 @@
+// Kernel templates: seeding, plain generation (u32 / uniform / normal), the
+// fused normal sum, and the stand-alone conversions.  Instantiated by the
+// xg_inst_*.cu translation units (one per parameter set) so that they compile
+// in parallel.
+#pragma once
+
+#include <type_traits>
+
+#include "xg_device.cuh"
+#include "xg_launch.h"
+
+namespace xg {
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+// Marsaglia's 64-bit xorshift, shift triple (13, 7, 17) ("Xorshift RNGs",
+// J. Stat. Software 8(14), 2003); expands a 32-bit seed.
+__device__ __forceinline__ uint64_t xorshift64(uint64_t v)
+{
+    v ^= v << 13;
+    v ^= v >> 7;
+    v ^= v << 17;
+    return v;
+}
+
+template <int TPG>
+__device__ __forceinline__ unsigned group_mask()
+{
+    if constexpr (TPG == 32) {
+        return 0xFFFFFFFFu;
+    } else {
+        const unsigned warp_lane = threadIdx.x & 31u;
+        return ((1u << TPG) - 1u) << (warp_lane & ~(unsigned)(TPG - 1));
+    }
+}
+
+// Load the 128-word ring of stream s: ring position p is window[base + p]
+// with base = kRingBase - pend.
+template <class E>
+__device__ __forceinline__ void load_ring(E& eng, const uint32_t* win_s, uint32_t pend)
+{
+    constexpr int W = E::WPL_;
+    const int base = kRingBase - (int)pend;
+    const uint32_t* p0 = win_s + base + W * eng.lane;
+    if constexpr (W % 4 == 0) {
+        if ((base & 3) == 0) {
+#pragma unroll
+            for (int t = 0; t < E::NROWS; ++t)
+#pragma unroll
+                for (int q = 0; q < W / 4; ++q) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(p0 + E::RW * t + 4 * q);
+                    eng.ring[t][4 * q + 0] = v.x;
+                    eng.ring[t][4 * q + 1] = v.y;
+                    eng.ring[t][4 * q + 2] = v.z;
+                    eng.ring[t][4 * q + 3] = v.w;
+                }
+            return;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < E::NROWS; ++t)
+#pragma unroll
+        for (int i = 0; i < W; ++i) eng.ring[t][i] = p0[E::RW * t + i];
+}
+
+// Store the window after a call: the retired row (the words just before the
+// ring) at [kWin - kR - RW, kWin - kR), then the ring rows, logical row t
+// being physical row (rot + t) mod NROWS.
+template <class E, int ROT>
+__device__ __forceinline__ void store_window_rot(const E& eng, uint32_t* win_s,
+                                                 const uint32_t (&retired)[E::WPL_])
+{
+    constexpr int W = E::WPL_;
+    uint32_t* p0 = win_s + (kWin - kR - E::RW) + W * eng.lane;
+    auto put = [&](uint32_t* p, const uint32_t(&v)[W]) {
+        if constexpr (W % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < W / 4; ++q)
+                *reinterpret_cast<uint4*>(p + 4 * q) =
+                    make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else if constexpr (W == 2) {
+            *reinterpret_cast<uint2*>(p) = make_uint2(v[0], v[1]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < W; ++i) p[i] = v[i];
+        }
+    };
+    put(p0, retired);
+#pragma unroll
+    for (int t = 0; t < E::NROWS; ++t) put(p0 + E::RW * (t + 1), eng.ring[(ROT + t) % E::NROWS]);
+}
+
+template <class E>
+__device__ __forceinline__ void store_window(const E& eng, uint32_t* win_s, int rot,
+                                             const uint32_t (&retired)[E::WPL_])
+{
+    if constexpr (E::NROWS == 4) {
+        switch (rot) {
+        case 0: store_window_rot<E, 0>(eng, win_s, retired); break;
+        case 1: store_window_rot<E, 1>(eng, win_s, retired); break;
+        case 2: store_window_rot<E, 2>(eng, win_s, retired); break;
+        default: store_window_rot<E, 3>(eng, win_s, retired); break;
+        }
+    } else {
+        if (rot == 0) store_window_rot<E, 0>(eng, win_s, retired);
+        else store_window_rot<E, 1>(eng, win_s, retired);
+    }
+}
+
+// Run nr rounds.  Full blocks of NROWS rounds go through emit.full(); the
+// last 1..NROWS rounds go through emit.tail() and the last one saves the row
+// it overwrites (the retired row).  Returns the final rotation.
+template <class E, class Emit>
+__device__ __forceinline__ int drive(E& eng, uint64_t nr, Emit& emit,
+                                     uint32_t (&retired)[E::WPL_])
+{
+    constexpr int W = E::WPL_;
+    uint64_t r = 0;
+    for (; r + E::NROWS < nr; r += E::NROWS) {
+        static_for<0, E::NROWS>([&](auto kc) {
+            constexpr int K = decltype(kc)::value;
+            eng.template round<K>();
+            emit.template full<K>(eng);
+        });
+    }
+    const int rem = (int)(nr - r);
+    static_for<0, E::NROWS>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        if (K < rem) {
+            if (K == rem - 1) {
+#pragma unroll
+                for (int i = 0; i < W; ++i) retired[i] = eng.ring[K][i];
+            }
+            eng.template round<K>();
+            emit.template tail<K>(eng, r + K);
+        }
+    });
+    return rem % E::NROWS;
+}
+
+// ---------------------------------------------------------------------------
+// Output emitters.  Word q of round t of a call has call offset RW*t + q and
+// Weyl value w_p + (RW*t + q + 1) * omega, w_p being the Weyl word at the
+// stream's consumed position.
+
+struct NoEmit {
+    template <int K, class E> __device__ __forceinline__ void full(const E&) {}
+    template <int K, class E> __device__ __forceinline__ void tail(const E&, uint64_t) {}
+};
+
+template <class E, int OUT, bool VEC>
+struct Emit {
+    static constexpr int W = E::WPL_;
+    static constexpr int RW = E::RW;
+    uint32_t* dst;     // this lane's first word of the current round
+    uint64_t limit;    // outputs wanted (normals: n, words otherwise)
+    uint64_t lane_off; // W * lane
+    uint32_t wl;       // Weyl word of this lane's element 0 in the current round
+    uint32_t omega;    // omega, or 0 with the Weyl generator off
+    float acc;         // fused sum
+
+    template <int K>
+    __device__ __forceinline__ void words(const E& eng, uint32_t (&o)[W])
+    {
+#pragma unroll
+        for (int i = 0; i < W; ++i) o[i] = combine(eng.ring[K][i], wl + (uint32_t)i * omega);
+        wl += (uint32_t)RW * omega;
+    }
+
+    template <int K>
+    __device__ __forceinline__ void full(const E& eng)
+    {
+        uint32_t o[W];
+        words<K>(eng, o);
+        uint32_t v[W];
+        convert(o, v);
+        if constexpr (OUT != kNormalSum) {
+            if constexpr (VEC && W % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < W / 4; ++q)
+                    *reinterpret_cast<uint4*>(dst + 4 * q) =
+                        make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else if constexpr (VEC && W == 2) {
+                *reinterpret_cast<uint2*>(dst) = make_uint2(v[0], v[1]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < W; ++i) dst[i] = v[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < W; ++i) acc = __fadd_rn(acc, __uint_as_float(v[i]));
+        }
+        dst += RW;
+    }
+
+    template <int K>
+    __device__ __forceinline__ void tail(const E& eng, uint64_t round)
+    {
+        uint32_t o[W];
+        words<K>(eng, o);
+        uint32_t v[W];
+        convert(o, v);
+        const uint64_t off = (uint64_t)RW * round + lane_off;
+        if constexpr (OUT != kNormalSum) {
+#pragma unroll
+            for (int i = 0; i < W; ++i)
+                if (off + i < limit) dst[i] = v[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < W; ++i)
+                if (off + i < limit) acc = __fadd_rn(acc, __uint_as_float(v[i]));
+        }
+        dst += RW;
+    }
+
+    __device__ __forceinline__ void convert(const uint32_t (&o)[W], uint32_t (&v)[W])
+    {
+        if constexpr (OUT == kU32) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) v[i] = o[i];
+        } else if constexpr (OUT == kUniform) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) v[i] = __float_as_uint(to_uniform(o[i]));
+        } else {
+            static_assert(W % 2 == 0, "normals pair words inside a lane");
+#pragma unroll
+            for (int i = 0; i < W; i += 2) {
+                float z1, z2;
+                normal_pair(o[i], o[i + 1], z1, z2);
+                v[i] = __float_as_uint(z1);
+                v[i + 1] = __float_as_uint(z2);
+            }
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+
+template <class P, int TPG, int WPL>
+__global__ void __launch_bounds__(256) seed_kernel(State st, const uint32_t* __restrict__ seeds,
+                                                   uint32_t first, uint32_t count)
+{
+    using E = Engine<P, TPG, WPL>;
+    const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) / TPG;
+    if (g >= count) return;
+    E eng;
+    eng.lane = threadIdx.x % TPG;
+    eng.mask = group_mask<TPG>();
+    const uint32_t seed = seeds[g];
+    uint64_t v = ((uint64_t)seed << 32) | (uint64_t)(~seed);
+    for (int j = 0; j < 64; ++j) v = xorshift64(v);
+    // ring position p = RW*t + WPL*lane + i takes the p-th of the next 128 outputs
+    uint32_t any = 0;
+    static_for<0, E::NROWS>([&](auto tc) {
+        constexpr int t = decltype(tc)::value;
+#pragma unroll
+        for (int u = 0; u < E::RW; ++u) {
+            v = xorshift64(v);
+            const uint32_t hi = (uint32_t)(v >> 32);
+            if (u / WPL == eng.lane) eng.ring[t][u % WPL] = hi;
+        }
+    });
+    v = xorshift64(v);
+    const uint32_t w0 = (uint32_t)(v >> 32);
+#pragma unroll
+    for (int t = 0; t < E::NROWS; ++t)
+#pragma unroll
+        for (int i = 0; i < WPL; ++i) any |= eng.ring[t][i];
+    any = __reduce_or_sync(eng.mask, any);
+    if (any == 0 && eng.lane == 0) eng.ring[0][0] = 1u;
+    // discard 4r words
+    NoEmit ne;
+    uint32_t retired[WPL];
+    const int rot = drive(eng, (uint64_t)(4 * kR / E::RW), ne, retired);
+    const uint32_t s = first + g;
+    __syncwarp(eng.mask);
+    store_window(eng, st.win + (uint64_t)s * kWin, rot, retired);
+    if (eng.lane == 0) {
+        st.weyl[s] = w0 + (uint32_t)(4 * kR) * kOmega;
+        st.pend[s] = 0;
+        st.pos[s] = 0;
+    }
+}
+
+template <class P, int TPG, int WPL, int OUT, bool VEC>
+__global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
+{
+    using E = Engine<P, TPG, WPL>;
+    constexpr int RW = E::RW;
+    const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) / TPG;
+    if (g >= a.nstreams) return;
+    E eng;
+    eng.lane = threadIdx.x % TPG;
+    eng.mask = group_mask<TPG>();
+    const uint32_t s = a.first + g;
+    constexpr bool kNormalOut = (OUT == kNormal || OUT == kNormalSum);
+    const uint64_t nwords = kNormalOut ? a.n + (a.n & 1u) : a.n;
+    Emit<E, OUT, VEC> em;
+    em.acc = 0.0f;
+    if (nwords > 0) {
+        uint32_t* win_s = a.st.win + (uint64_t)s * kWin;
+        const uint32_t pend = a.st.pend[s];
+        const uint32_t wp = a.st.weyl[s];
+        load_ring(eng, win_s, pend);
+        em.omega = a.omega;
+        em.limit = a.n;
+        em.lane_off = (uint64_t)WPL * eng.lane;
+        em.wl = wp + (uint32_t)(WPL * eng.lane + 1) * a.omega;
+        em.dst = (OUT == kNormalSum) ? nullptr
+                                     : reinterpret_cast<uint32_t*>(a.out) + (uint64_t)g * a.ld + em.lane_off;
+        uint32_t retired[WPL];
+        const uint64_t nr = (nwords + RW - 1) / RW;
+        const int rot = drive(eng, nr, em, retired);
+        __syncwarp(eng.mask);
+        store_window(eng, win_s, rot, retired);
+        if (eng.lane == 0) {
+            a.st.weyl[s] = wp + (uint32_t)nwords * a.omega;
+            a.st.pend[s] = (uint32_t)(nr * RW - nwords);
+            a.st.pos[s] += nwords;
+        }
+    }
+    if constexpr (OUT == kNormalSum) {
+        float acc = em.acc;
+#pragma unroll
+        for (int off = TPG / 2; off >= 1; off /= 2)
+            acc = __fadd_rn(acc, __shfl_xor_sync(eng.mask, acc, off, TPG));
+        if (eng.lane == 0) a.sums[g] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers, instantiated per parameter set.
+
+template <class P, int TPG, int WPL>
+cudaError_t launch_seed_impl(const State& st, const uint32_t* d_seeds, uint32_t first,
+                             uint32_t count, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    constexpr int block = 128;
+    const uint64_t threads = (uint64_t)count * TPG;
+    const unsigned grid = (unsigned)((threads + block - 1) / block);
+    seed_kernel<P, TPG, WPL><<<grid, block, 0, s>>>(st, d_seeds, first, count);
+    return cudaGetLastError();
+}
+
+template <class P, int TPG, int WPL, int OUT, bool VEC>
+cudaError_t launch_gen_one(int block, const GenArgs& a, cudaStream_t s)
+{
+    const uint64_t threads = (uint64_t)a.nstreams * TPG;
+    const unsigned grid = (unsigned)((threads + block - 1) / block);
+    gen_kernel<P, TPG, WPL, OUT, VEC><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class P, int TPG, int WPL>
+cudaError_t launch_gen_cfg(int out_kind, bool vec, int block, const GenArgs& a, cudaStream_t s)
+{
+    switch (out_kind) {
+    case kU32:
+        return vec ? launch_gen_one<P, TPG, WPL, kU32, true>(block, a, s)
+                   : launch_gen_one<P, TPG, WPL, kU32, false>(block, a, s);
+    case kUniform:
+        return vec ? launch_gen_one<P, TPG, WPL, kUniform, true>(block, a, s)
+                   : launch_gen_one<P, TPG, WPL, kUniform, false>(block, a, s);
+    case kNormal:
+        return vec ? launch_gen_one<P, TPG, WPL, kNormal, true>(block, a, s)
+                   : launch_gen_one<P, TPG, WPL, kNormal, false>(block, a, s);
+    case kNormalSum:
+        return launch_gen_one<P, TPG, WPL, kNormalSum, true>(block, a, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <class P>
+cudaError_t launch_gen_impl(int cfg, int out_kind, bool vec, int block, const GenArgs& a,
+                            cudaStream_t s)
+{
+    if (a.nstreams == 0) return cudaSuccess;
+    switch (cfg) {
+    case 0: return launch_gen_cfg<P, 4, 8>(out_kind, vec, block, a, s);
+    case 1: return launch_gen_cfg<P, 8, 4>(out_kind, vec, block, a, s);
+    case 2: return launch_gen_cfg<P, 16, 2>(out_kind, vec, block, a, s);
+    case 3: return launch_gen_cfg<P, 16, 4>(out_kind, vec, block, a, s);
+    case 4: return launch_gen_cfg<P, 32, 2>(out_kind, vec, block, a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace xg

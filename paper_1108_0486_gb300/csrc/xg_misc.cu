@@ -1,0 +1,84 @@
+// Stand-alone conversion kernels and the parameter-set dispatch.
+#include "xg_device.cuh"
+#include "xg_launch.h"
+
+namespace xg {
+
+const LaunchCfg kCfgs[kNumCfgs] = {{4, 8, 64}, {8, 4, 64}, {16, 2, 64}, {16, 4, 64}, {32, 2, 64}};
+
+int cfg_index(int tpg, int wpl)
+{
+    for (int i = 0; i < kNumCfgs; ++i)
+        if (kCfgs[i].tpg == tpg && kCfgs[i].wpl == wpl) return i;
+    return -1;
+}
+
+// Uniform conversion of n words, 4 per thread when both buffers are 16-byte
+// aligned (vec), one per thread otherwise.
+__global__ void __launch_bounds__(256) transform_uniform_kernel(const uint32_t* __restrict__ in,
+                                                                 uint64_t n, float* __restrict__ out,
+                                                                 bool vec)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n4 = vec ? n / 4 : 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const uint4 w = reinterpret_cast<const uint4*>(in)[i];
+        reinterpret_cast<float4*>(out)[i] =
+            make_float4(to_uniform(w.x), to_uniform(w.y), to_uniform(w.z), to_uniform(w.w));
+    }
+    for (uint64_t i = 4 * n4 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = to_uniform(in[i]);
+}
+
+// Box-Muller on pairs (in[2i], in[2i+1]) -> (out[2i], out[2i+1]).
+__global__ void __launch_bounds__(256) transform_normal_kernel(const uint32_t* __restrict__ in,
+                                                                uint64_t npairs, float* __restrict__ out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+        const uint2 w = reinterpret_cast<const uint2*>(in)[i];
+        float z1, z2;
+        normal_pair(w.x, w.y, z1, z2);
+        reinterpret_cast<float2*>(out)[i] = make_float2(z1, z2);
+    }
+}
+
+cudaError_t launch_transform(int out_kind, const uint32_t* in, uint64_t n, float* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int block = 256;
+    if (out_kind == kUniform) {
+        const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+        uint64_t work = aligned ? (n + 3) / 4 : n;
+        uint64_t grid = (work + block - 1) / block;
+        if (grid > (uint64_t)sms * 16) grid = (uint64_t)sms * 16;
+        transform_uniform_kernel<<<(unsigned)grid, block, 0, s>>>(in, n, out, aligned);
+    } else if (out_kind == kNormal) {
+        const uint64_t npairs = n / 2;
+        uint64_t grid = (npairs + block - 1) / block;
+        if (grid > (uint64_t)sms * 16) grid = (uint64_t)sms * 16;
+        transform_normal_kernel<<<(unsigned)grid, block, 0, s>>>(in, npairs, out);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed(int param_set, const State& st, const uint32_t* d_seeds, uint32_t first,
+                        uint32_t count, cudaStream_t s)
+{
+    return param_set == 1 ? launch_seed_paper(st, d_seeds, first, count, s)
+                          : launch_seed_default(st, d_seeds, first, count, s);
+}
+
+cudaError_t launch_gen(int param_set, int cfg, int out_kind, bool vec, int block, const GenArgs& a,
+                       cudaStream_t s)
+{
+    return param_set == 1 ? launch_gen_paper(cfg, out_kind, vec, block, a, s)
+                          : launch_gen_default(cfg, out_kind, vec, block, a, s);
+}
+
+}  // namespace xg

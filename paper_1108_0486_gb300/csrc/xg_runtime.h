@@ -1,0 +1,43 @@
+// The library's context object (the C ABI's opaque xg_ctx).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "xg_launch.h"
+#include "xorgens_gb300.h"
+
+namespace xg {
+class Server;
+}
+
+struct xg_ctx {
+    int device = 0;
+    int sm_count = 148;
+    uint32_t n = 0;            // streams
+    uint32_t param_set = 0;    // 0: (128,95,17,12,13,15), 1: (128,65,15,14,12,17)
+    uint32_t weyl_on = 1;
+    cudaStream_t stream = nullptr;  // caller-owned
+    void* state_mem = nullptr;
+    xg::State st{};
+    int cfg[3] = {-1, -1, -1};      // per output type; -1 = automatic
+    int block[xg::kNumCfgs] = {};   // threads per block per configuration
+    // host-output staging
+    void* staging[2] = {nullptr, nullptr};
+    size_t staging_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_gen[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
+    std::mutex mu;
+    xg::Server* server = nullptr;
+
+    int pick_cfg(int kind, uint32_t nstreams) const;
+    xg_status ensure_staging(size_t bytes);
+    void shutdown_server();
+};
+
+namespace xg {
+using Ctx = xg_ctx;
+}
