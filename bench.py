@@ -51,6 +51,25 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _traffic():
+    """ncu DRAM bytes per launch of the dominant kernel, if recorded for the
+    current kernel sources (else None)."""
+    import hashlib
+    try:
+        rec = {}
+        for line in open(os.path.join(ROOT, "profiles", "gen_kernel_traffic.txt")):
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                rec[k] = v
+        src = b"".join(open(os.path.join(ROOT, "paper_1108_0486_gb300", "csrc", f), "rb").read()
+                       for f in ("xg_device.cuh", "xg_kernels.cuh"))
+        if hashlib.sha256(src).hexdigest()[:16] != rec.get("kernel_sources_sha256_16"):
+            return None
+        return float(rec["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -261,7 +280,7 @@ def run_ours(args):
     achieved = bytes_per_launch / (dom_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": args.traffic,
+                "traffic": args.traffic if args.traffic is not None else _traffic(),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "per_kernel_ms": {"u32": avg_u, "uniform": avg_f}}
 
@@ -358,11 +377,18 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the extra rows")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-per", type=int, default=None,
+                    help="override words per stream (profiling of a smaller case; not a bench line)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.n_per:
+        global N_PER
+        N_PER = args.n_per
+        CONFIG["n_per_stream"] = N_PER
+        CONFIG["workload"] = f"PROFILING CASE: {STREAMS} streams x {N_PER} words (not the bench workload)"
     if args.impl == "reference":
         run_reference(args)
     else:

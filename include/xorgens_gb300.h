@@ -135,6 +135,90 @@ xg_status xg_generate_normal_sum(xg_ctx* ctx, uint32_t first, uint32_t nstreams,
 xg_status xg_transform_uniform(xg_ctx* ctx, const uint32_t* d_words, uint64_t n, float* d_out);
 xg_status xg_transform_normal(xg_ctx* ctx, const uint32_t* d_words, uint64_t n, float* d_out);
 
+/* ---- batched generation ------------------------------------------------ */
+
+typedef struct {
+    uint32_t stream; /* stream index in the context */
+    uint32_t type;   /* xg_type */
+    uint64_t count;  /* outputs */
+    void* out;       /* device memory for count 4-byte outputs (16-byte
+                        alignment takes the vector-store path) */
+} xg_item;
+
+/* Run n_items generation calls with ONE launch of the persistent batch
+ * kernel, replayed from a CUDA graph (a copy of the batch description into
+ * device scratch, then the kernel).  Items may have different types and very
+ * different lengths.  Items of the same stream run in array order, exactly as
+ * consecutive xg_generate_* calls would; different streams run concurrently,
+ * one warp per stream, the longest stream first.  Asynchronous on the
+ * context's stream; the items array may be reused when the call returns.
+ * This is the independent-subsequence scheme of Sec. 2: each stream is one
+ * generator with its own state. */
+xg_status xg_generate_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items);
+
+/* ---- serving: continuous batching of requests --------------------------- */
+
+typedef struct {
+    uint64_t mem_cap_bytes; /* cap on outstanding output bytes (pool buffers and
+                               caller buffers alike); 0 = 16 GiB.  The pool is
+                               one device allocation of this size. */
+    uint32_t max_batch;     /* requests per batch launch; 0 = 1024 */
+    uint32_t lanes;         /* batches in flight at once, each on its own CUDA
+                               stream; 0 = 16, at most 64 */
+} xg_server_config;
+
+typedef struct {
+    uint32_t stream; /* stream index in the context */
+    uint32_t type;   /* xg_type */
+    uint64_t count;  /* outputs (> 0) */
+    void* d_out;     /* device memory for count outputs, or NULL: the library
+                        carves a buffer from its pool, valid until xg_release */
+} xg_request;
+
+typedef struct {
+    uint64_t submitted, completed, refused, queued, in_flight, batches, items_launched;
+    uint64_t outstanding_bytes;
+    uint64_t now_ns; /* the server clock (steady, ns) that xg_ticket_times uses */
+} xg_server_stats;
+
+/* Start the request server on a context.  From then on the context's streams
+ * belong to the server: plain generate, seed and set_state calls return
+ * XG_EINVAL until xg_server_stop.  A host thread admits requests, keeps a
+ * FIFO per stream (a stream has at most one request on the GPU, so its
+ * requests run in submission order and read consecutive words), and whenever
+ * one of the lanes is free launches the oldest ready requests as one batch
+ * (one replay of the persistent batch kernel's graph).  Batches on different
+ * lanes run concurrently, so requests that arrive while others are on the
+ * GPU start as soon as a lane and memory free up.  Each result is identical
+ * to the same request run alone. */
+xg_status xg_server_start(xg_ctx* ctx, const xg_server_config* cfg);
+
+/* Stop the server thread after the batches in flight finish; frees the pool
+ * (pool results become invalid). */
+xg_status xg_server_stop(xg_ctx* ctx);
+
+/* Non-blocking.  XG_EAGAIN when admitting the request would put the
+ * outstanding output bytes above the cap (retry later, after xg_release). */
+xg_status xg_submit(xg_ctx* ctx, const xg_request* req, uint64_t* ticket);
+
+/* Non-blocking.  *done = 1 once the request's outputs are in device memory
+ * and visible to later work on any stream; *d_result is then its output
+ * pointer.  XG_EDEVICE if the request's batch failed to run. */
+xg_status xg_poll(xg_ctx* ctx, uint64_t ticket, int* done, void** d_result);
+
+/* Poll until done or timeout_ms elapses (XG_ETIMEDOUT). */
+xg_status xg_wait(xg_ctx* ctx, uint64_t ticket, uint32_t timeout_ms, void** d_result);
+
+/* Forget a finished ticket and return its bytes (and pool buffer) to the cap. */
+xg_status xg_release(xg_ctx* ctx, uint64_t ticket);
+
+/* Server clock timestamps of a ticket: submission, batch launch, completion
+ * as seen by the host (0 while pending). */
+xg_status xg_ticket_times(xg_ctx* ctx, uint64_t ticket, uint64_t* t_submit_ns,
+                          uint64_t* t_launch_ns, uint64_t* t_done_ns);
+
+xg_status xg_server_stats_get(xg_ctx* ctx, xg_server_stats* out);
+
 /* ---- launch configuration --------------------------------------------- */
 
 /* Threads per generator (tpg) and words per thread per round (wpl) used for

@@ -32,6 +32,27 @@ u32, u64, vp, i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_
 P_u32, P_u64, P_vp, P_i32 = (ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int))
 
+class XgItem(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_uint32), ("type", ctypes.c_uint32),
+                ("count", ctypes.c_uint64), ("out", ctypes.c_void_p)]
+
+
+class XgRequest(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_uint32), ("type", ctypes.c_uint32),
+                ("count", ctypes.c_uint64), ("d_out", ctypes.c_void_p)]
+
+
+class XgServerConfig(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("lanes", ctypes.c_uint32)]
+
+
+class XgServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "submitted", "completed", "refused", "queued", "in_flight", "batches", "items_launched",
+        "outstanding_bytes", "now_ns")]
+
+
 # name -> argtypes (all return xg_status unless listed in _RESTYPES)
 SIGNATURES = {
     "xg_create_streams": [P_vp, u32, u32, u32, vp],
@@ -47,6 +68,15 @@ SIGNATURES = {
     "xg_generate_normal_sum": [vp, u32, u32, u64, vp],
     "xg_transform_uniform": [vp, vp, u64, vp],
     "xg_transform_normal": [vp, vp, u64, vp],
+    "xg_generate_batch": [vp, vp, u32],
+    "xg_server_start": [vp, vp],
+    "xg_server_stop": [vp],
+    "xg_submit": [vp, vp, P_u64],
+    "xg_poll": [vp, u64, P_i32, P_vp],
+    "xg_wait": [vp, u64, u32, P_vp],
+    "xg_release": [vp, u64],
+    "xg_ticket_times": [vp, u64, P_u64, P_u64, P_u64],
+    "xg_server_stats_get": [vp, vp],
     "xg_set_launch": [vp, i32, u32, u32],
     "xg_get_launch": [vp, i32, P_u32, P_u32],
     "xg_last_error": [],
@@ -145,6 +175,56 @@ def xg_transform_uniform(ctx, words_ptr, n, out_ptr) -> None:
 
 def xg_transform_normal(ctx, words_ptr, n, out_ptr) -> None:
     call("xg_transform_normal", ctypes.c_void_p(ctx), ctypes.c_void_p(words_ptr), n, ctypes.c_void_p(out_ptr))
+
+
+def xg_generate_batch(ctx, items) -> None:
+    """items: sequence of (stream, type, count, out_ptr)."""
+    arr = (XgItem * len(items))(*[XgItem(s, t, c, o) for s, t, c, o in items])
+    call("xg_generate_batch", ctypes.c_void_p(ctx), arr, len(items))
+
+
+def xg_server_start(ctx, mem_cap_bytes=0, max_batch=0, lanes=0) -> None:
+    cfg = XgServerConfig(mem_cap_bytes, max_batch, lanes)
+    call("xg_server_start", ctypes.c_void_p(ctx), ctypes.byref(cfg))
+
+
+def xg_server_stop(ctx) -> None:
+    call("xg_server_stop", ctypes.c_void_p(ctx))
+
+
+def xg_submit(ctx, stream, out_type, count, d_out=0) -> int:
+    req = XgRequest(stream, out_type, count, d_out)
+    t = ctypes.c_uint64()
+    call("xg_submit", ctypes.c_void_p(ctx), ctypes.byref(req), ctypes.byref(t))
+    return t.value
+
+
+def xg_poll(ctx, ticket):
+    done, ptr = ctypes.c_int(), ctypes.c_void_p()
+    call("xg_poll", ctypes.c_void_p(ctx), ticket, ctypes.byref(done), ctypes.byref(ptr))
+    return bool(done.value), ptr.value
+
+
+def xg_wait(ctx, ticket, timeout_ms=10000):
+    ptr = ctypes.c_void_p()
+    call("xg_wait", ctypes.c_void_p(ctx), ticket, timeout_ms, ctypes.byref(ptr))
+    return ptr.value
+
+
+def xg_release(ctx, ticket) -> None:
+    call("xg_release", ctypes.c_void_p(ctx), ticket)
+
+
+def xg_ticket_times(ctx, ticket):
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    call("xg_ticket_times", ctypes.c_void_p(ctx), ticket, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value
+
+
+def xg_server_stats_get(ctx) -> dict:
+    st = XgServerStats()
+    call("xg_server_stats_get", ctypes.c_void_p(ctx), ctypes.byref(st))
+    return {n: getattr(st, n) for n, _ in XgServerStats._fields_}
 
 
 def xg_set_launch(ctx, out_type, tpg, wpl) -> None:

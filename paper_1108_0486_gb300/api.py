@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 import torch
+import torch.utils.dlpack
 
 from . import _lib as L
 
@@ -118,6 +119,115 @@ class Streams:
         out = torch.empty(words.numel(), dtype=torch.float32, device="cuda") if out is None else out
         L.xg_transform_normal(self.ctx, words.data_ptr(), words.numel(), out.data_ptr())
         return out
+
+
+    # ---- batches and serving -------------------------------------------
+    def batch(self, items):
+        """One persistent-kernel launch for items (stream, kind, count, out)
+        with out a device tensor (or None for count 0)."""
+        L.xg_generate_batch(self.ctx, [(int(s), TYPES[k] if isinstance(k, str) else int(k), int(c),
+                                        0 if o is None else o.data_ptr()) for s, k, c, o in items])
+
+    def serve(self, mem_cap_bytes: int = 0, max_batch: int = 0, lanes: int = 0) -> "Server":
+        return Server(self, mem_cap_bytes, max_batch, lanes)
+
+
+class Server:
+    """The request server of a Streams context (continuous batching)."""
+
+    def __init__(self, streams: Streams, mem_cap_bytes=0, max_batch=0, lanes=0):
+        self.streams = streams
+        self.ctx = streams.ctx
+        L.xg_server_start(self.ctx, mem_cap_bytes, max_batch, lanes)
+        self.running = True
+
+    def submit(self, stream: int, kind, count: int, out: torch.Tensor | None = None) -> int:
+        t = TYPES[kind] if isinstance(kind, str) else int(kind)
+        return L.xg_submit(self.ctx, stream, t, count, 0 if out is None else out.data_ptr())
+
+    def poll(self, ticket: int):
+        return L.xg_poll(self.ctx, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = 10000) -> int:
+        return L.xg_wait(self.ctx, ticket, timeout_ms)
+
+    def release(self, ticket: int):
+        L.xg_release(self.ctx, ticket)
+
+    def times(self, ticket: int):
+        return L.xg_ticket_times(self.ctx, ticket)
+
+    def stats(self) -> dict:
+        return L.xg_server_stats_get(self.ctx)
+
+    def result(self, ticket: int, kind, count: int, timeout_ms: int = 10000) -> torch.Tensor:
+        """Wait for a ticket and view its output as a tensor (no copy)."""
+        ptr = self.wait(ticket, timeout_ms)
+        dt = torch.int32 if (kind == "u32" or kind == L.XG_U32) else torch.float32
+        return device_view(ptr, count, dt)
+
+    def stop(self):
+        if self.running:
+            L.xg_server_stop(self.ctx)
+            self.running = False
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
+
+
+# ---- DLPack view of library-owned device memory ------------------------------
+import ctypes as _ct
+
+
+class _DLDevice(_ct.Structure):
+    _fields_ = [("device_type", _ct.c_int), ("device_id", _ct.c_int)]
+
+
+class _DLDataType(_ct.Structure):
+    _fields_ = [("code", _ct.c_uint8), ("bits", _ct.c_uint8), ("lanes", _ct.c_uint16)]
+
+
+class _DLTensor(_ct.Structure):
+    _fields_ = [("data", _ct.c_void_p), ("device", _DLDevice), ("ndim", _ct.c_int),
+                ("dtype", _DLDataType), ("shape", _ct.POINTER(_ct.c_int64)),
+                ("strides", _ct.POINTER(_ct.c_int64)), ("byte_offset", _ct.c_uint64)]
+
+
+_DELETER = _ct.CFUNCTYPE(None, _ct.c_void_p)
+
+
+class _DLManagedTensor(_ct.Structure):
+    _fields_ = [("dl_tensor", _DLTensor), ("manager_ctx", _ct.c_void_p), ("deleter", _DELETER)]
+
+
+_keep = {}
+
+
+@_DELETER
+def _dl_deleter(p):
+    _keep.pop(p, None)
+
+
+def device_view(ptr: int, count: int, dtype=torch.float32) -> torch.Tensor:
+    """A 1-D tensor over `count` 4-byte elements at device pointer ptr.  The
+    memory stays owned by the library (valid until the ticket is released)."""
+    code = 0 if dtype == torch.int32 else 2  # kDLInt / kDLFloat
+    shape = (_ct.c_int64 * 1)(count)
+    mt = _DLManagedTensor()
+    mt.dl_tensor = _DLTensor(ptr, _DLDevice(2, torch.cuda.current_device()), 1,
+                             _DLDataType(code, 32, 1), shape, None, 0)
+    mt.manager_ctx = None
+    mt.deleter = _dl_deleter
+    addr = _ct.addressof(mt)
+    _keep[addr] = (mt, shape)
+    PyCapsule_New = _ct.pythonapi.PyCapsule_New
+    PyCapsule_New.restype = _ct.py_object
+    PyCapsule_New.argtypes = [_ct.c_void_p, _ct.c_char_p, _ct.c_void_p]
+    cap = PyCapsule_New(addr, b"dltensor", None)
+    return torch.utils.dlpack.from_dlpack(cap)
 
 
 def as_u32(t: torch.Tensor) -> np.ndarray:

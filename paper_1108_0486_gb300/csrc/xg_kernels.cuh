@@ -289,49 +289,118 @@ __global__ void __launch_bounds__(256) seed_kernel(State st, const uint32_t* __r
     }
 }
 
+// One call on one stream s: n outputs of kind OUT written to row (this
+// stream's first output), the stream state read at the start and written
+// back at the end.  Returns the lane's partial sum for kNormalSum.
 template <class P, int TPG, int WPL, int OUT, bool VEC>
-__global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
+__device__ __forceinline__ float run_stream(const State& st, uint32_t s, uint64_t n, uint32_t* row,
+                                            uint32_t omega, int lane, unsigned mask)
 {
     using E = Engine<P, TPG, WPL>;
     constexpr int RW = E::RW;
-    const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) / TPG;
-    if (g >= a.nstreams) return;
-    E eng;
-    eng.lane = threadIdx.x % TPG;
-    eng.mask = group_mask<TPG>();
-    const uint32_t s = a.first + g;
     constexpr bool kNormalOut = (OUT == kNormal || OUT == kNormalSum);
-    const uint64_t nwords = kNormalOut ? a.n + (a.n & 1u) : a.n;
+    const uint64_t nwords = kNormalOut ? n + (n & 1u) : n;
     Emit<E, OUT, VEC> em;
     em.acc = 0.0f;
-    if (nwords > 0) {
-        uint32_t* win_s = a.st.win + (uint64_t)s * kWin;
-        const uint32_t pend = a.st.pend[s];
-        const uint32_t wp = a.st.weyl[s];
-        load_ring(eng, win_s, pend);
-        em.omega = a.omega;
-        em.limit = a.n;
-        em.lane_off = (uint64_t)WPL * eng.lane;
-        em.wl = wp + (uint32_t)(WPL * eng.lane + 1) * a.omega;
-        em.dst = (OUT == kNormalSum) ? nullptr
-                                     : reinterpret_cast<uint32_t*>(a.out) + (uint64_t)g * a.ld + em.lane_off;
-        uint32_t retired[WPL];
-        const uint64_t nr = (nwords + RW - 1) / RW;
-        const int rot = drive(eng, nr, em, retired);
-        __syncwarp(eng.mask);
-        store_window(eng, win_s, rot, retired);
-        if (eng.lane == 0) {
-            a.st.weyl[s] = wp + (uint32_t)nwords * a.omega;
-            a.st.pend[s] = (uint32_t)(nr * RW - nwords);
-            a.st.pos[s] += nwords;
-        }
+    if (nwords == 0) return 0.0f;
+    E eng;
+    eng.lane = lane;
+    eng.mask = mask;
+    uint32_t* win_s = st.win + (uint64_t)s * kWin;
+    const uint32_t pend = st.pend[s];
+    const uint32_t wp = st.weyl[s];
+    load_ring(eng, win_s, pend);
+    em.omega = omega;
+    em.limit = n;
+    em.lane_off = (uint64_t)WPL * lane;
+    em.wl = wp + (uint32_t)(WPL * lane + 1) * omega;
+    em.dst = (OUT == kNormalSum) ? nullptr : row + em.lane_off;
+    uint32_t retired[WPL];
+    const uint64_t nr = (nwords + RW - 1) / RW;
+    const int rot = drive(eng, nr, em, retired);
+    __syncwarp(mask);
+    store_window(eng, win_s, rot, retired);
+    if (lane == 0) {
+        st.weyl[s] = wp + (uint32_t)nwords * omega;
+        st.pend[s] = (uint32_t)(nr * RW - nwords);
+        st.pos[s] += nwords;
     }
+    return em.acc;
+}
+
+template <class P, int TPG, int WPL, int OUT, bool VEC>
+__global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
+{
+    const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) / TPG;
+    if (g >= a.nstreams) return;
+    const int lane = threadIdx.x % TPG;
+    const unsigned mask = group_mask<TPG>();
+    uint32_t* row = (OUT == kNormalSum) ? nullptr
+                                        : reinterpret_cast<uint32_t*>(a.out) + (uint64_t)g * a.ld;
+    float acc = run_stream<P, TPG, WPL, OUT, VEC>(a.st, a.first + g, a.n, row, a.omega, lane, mask);
     if constexpr (OUT == kNormalSum) {
-        float acc = em.acc;
 #pragma unroll
         for (int off = TPG / 2; off >= 1; off /= 2)
-            acc = __fadd_rn(acc, __shfl_xor_sync(eng.mask, acc, off, TPG));
-        if (eng.lane == 0) a.sums[g] = acc;
+            acc = __fadd_rn(acc, __shfl_xor_sync(mask, acc, off, TPG));
+        if (lane == 0) a.sums[g] = acc;
+    }
+}
+
+// Persistent batch kernel.  Each warp repeatedly takes the next chain head
+// (atomic counter; heads are sorted longest first by the host), then runs
+// every item of that chain -- the calls on one stream, in order -- with 32
+// lanes per stream and 64-word rounds.  Item types may differ.  When an item
+// has a completion flag, the warp fences its stores system-wide and sets
+// the flag to 1.
+template <class P>
+__device__ __forceinline__ void run_item(const State& st, const BatchItem& it, uint32_t omega, int lane)
+{
+    uint32_t* row = reinterpret_cast<uint32_t*>(it.out);
+    const bool vec = (reinterpret_cast<uintptr_t>(row) & 15u) == 0;
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    switch (it.kind) {
+    case kU32:
+        if (vec) run_stream<P, 32, 2, kU32, true>(st, it.stream, it.count, row, omega, lane, kFull);
+        else run_stream<P, 32, 2, kU32, false>(st, it.stream, it.count, row, omega, lane, kFull);
+        break;
+    case kUniform:
+        if (vec) run_stream<P, 32, 2, kUniform, true>(st, it.stream, it.count, row, omega, lane, kFull);
+        else run_stream<P, 32, 2, kUniform, false>(st, it.stream, it.count, row, omega, lane, kFull);
+        break;
+    default:
+        if (vec) run_stream<P, 32, 2, kNormal, true>(st, it.stream, it.count, row, omega, lane, kFull);
+        else run_stream<P, 32, 2, kNormal, false>(st, it.stream, it.count, row, omega, lane, kFull);
+        break;
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) batch_kernel(BatchArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    BatchHeader* hdr = a.hdr;
+    const uint32_t n_heads = hdr->n_heads;
+    const uint32_t* heads = reinterpret_cast<const uint32_t*>(hdr + 1);
+    const BatchItem* items = reinterpret_cast<const BatchItem*>(
+        reinterpret_cast<const char*>(hdr) + batch_items_offset(hdr->capacity));
+    for (;;) {
+        uint32_t h = 0;
+        if (lane == 0) h = atomicAdd(&hdr->counter, 1u);
+        h = __shfl_sync(kFull, h, 0);
+        if (h >= n_heads) break;
+        uint32_t idx = heads[h];
+        while (idx != kNoItem) {
+            const BatchItem it = items[idx];
+            run_item<P>(a.st, it, a.omega, lane);
+            __syncwarp(kFull);
+            if (it.flag) {
+                __threadfence_system();
+                __syncwarp(kFull);
+                if (lane == 0) *reinterpret_cast<volatile uint32_t*>(it.flag) = 1u;
+            }
+            idx = it.next;
+        }
     }
 }
 
@@ -377,6 +446,19 @@ cudaError_t launch_gen_cfg(int out_kind, bool vec, int block, const GenArgs& a, 
     default:
         return cudaErrorInvalidValue;
     }
+}
+
+template <class P>
+cudaError_t launch_batch_impl(const BatchArgs& a, unsigned grid, cudaStream_t s)
+{
+    batch_kernel<P><<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class P>
+const void* batch_kernel_ptr()
+{
+    return reinterpret_cast<const void*>(&batch_kernel<P>);
 }
 
 template <class P>

@@ -2,8 +2,15 @@
 // units.  Plain C++ (no device code), included by both sides.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#if defined(__CUDACC__)
+#define XG_HD __host__ __device__
+#else
+#define XG_HD
+#endif
 
 namespace xg {
 
@@ -36,6 +43,43 @@ struct GenArgs {
     uint32_t omega;     // Weyl increment, 0 when the Weyl generator is off
 };
 
+// ---- batches: work items of the persistent batch kernel -----------------
+constexpr uint32_t kNoItem = 0xFFFFFFFFu;
+
+struct BatchItem {
+    uint32_t stream;   // stream index in the context
+    uint32_t kind;     // kU32, kUniform or kNormal
+    uint64_t count;    // outputs
+    void* out;         // device output (count 4-byte elements)
+    uint32_t* flag;    // device-visible completion flag, or null
+    uint32_t next;     // next item of the same stream (kNoItem: none)
+    uint32_t pad;
+};
+
+// Scratch layout of one batch: header, chain heads (u32, longest chain
+// first), then the items at batch_items_offset(capacity).
+struct BatchHeader {
+    uint32_t counter;   // next head to take (reset to 0 by every launch)
+    uint32_t n_heads;
+    uint32_t n_items;
+    uint32_t capacity;  // items the scratch can hold
+};
+
+XG_HD inline size_t batch_items_offset(uint32_t capacity)
+{
+    return (sizeof(BatchHeader) + (size_t)capacity * 4 + 15) / 16 * 16;
+}
+XG_HD inline size_t batch_scratch_bytes(uint32_t capacity)
+{
+    return batch_items_offset(capacity) + (size_t)capacity * sizeof(BatchItem);
+}
+
+struct BatchArgs {
+    State st;
+    BatchHeader* hdr;   // device scratch
+    uint32_t omega;
+};
+
 // Launch configurations: lanes per generator (tpg) x words per lane (wpl).
 struct LaunchCfg {
     int tpg;
@@ -54,10 +98,17 @@ cudaError_t launch_gen(int param_set, int cfg, int out_kind, bool vec, int block
 cudaError_t launch_transform(int out_kind, const uint32_t* in, uint64_t n, float* out,
                              cudaStream_t s);
 
+cudaError_t launch_batch(int param_set, const BatchArgs& a, unsigned grid, cudaStream_t s);
+const void* batch_kernel_ptr(int param_set);
+
 // Per parameter set (defined in xg_inst_default.cu / xg_inst_paper.cu).
 cudaError_t launch_seed_default(const State&, const uint32_t*, uint32_t, uint32_t, cudaStream_t);
 cudaError_t launch_seed_paper(const State&, const uint32_t*, uint32_t, uint32_t, cudaStream_t);
 cudaError_t launch_gen_default(int cfg, int out_kind, bool vec, int block, const GenArgs&, cudaStream_t);
 cudaError_t launch_gen_paper(int cfg, int out_kind, bool vec, int block, const GenArgs&, cudaStream_t);
+cudaError_t launch_batch_default(const BatchArgs&, unsigned grid, cudaStream_t);
+cudaError_t launch_batch_paper(const BatchArgs&, unsigned grid, cudaStream_t);
+const void* batch_kernel_ptr_default();
+const void* batch_kernel_ptr_paper();
 
 }  // namespace xg

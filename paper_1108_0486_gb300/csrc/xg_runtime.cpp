@@ -12,12 +12,15 @@
 #include <string>
 #include <vector>
 
+#include "xg_batch.h"
 #include "xg_launch.h"
 #include "xg_runtime.h"
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace xg {
 
 xg_status fail(xg_status st, const char* fmt, ...)
 {
@@ -34,6 +37,13 @@ xg_status cuda_fail(cudaError_t e, const char* what)
 {
     return fail(XG_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
+
+}  // namespace xg
+
+using xg::fail;
+using xg::cuda_fail;
+
+namespace {
 
 #define XG_CUDA(call, what)                        \
     do {                                           \
@@ -166,6 +176,7 @@ static xg_status generate_common(xg_ctx* ctx, int kind, uint32_t first, uint32_t
     if (nstreams == 1 && ld < n) ld = n;
     if (ld > (UINT64_MAX / 8) / nstreams) return fail(XG_EINVAL, "output extent overflows");
     if (reinterpret_cast<uintptr_t>(out) & 3u) return fail(XG_EINVAL, "output must be 4-byte aligned");
+    if (c->server) return fail(XG_EINVAL, "the request server owns this context; use xg_submit");
     std::lock_guard<std::mutex> lk(c->mu);
     if (is_device_pointer(out)) return enqueue_gen(c, kind, first, nstreams, n, out, ld, nullptr, c->stream);
     return generate_to_host(c, kind, first, nstreams, n, out, ld);
@@ -232,6 +243,10 @@ xg_status xg_destroy(xg_ctx* ctx)
     if (!ctx) return XG_OK;
     Ctx* c = ctx;
     c->shutdown_server();
+    for (int b = 0; b < 2; ++b) {
+        delete c->batch[b];
+        c->batch[b] = nullptr;
+    }
     if (c->stream || c->state_mem) cudaStreamSynchronize(c->stream);
     if (c->copy_stream) {
         cudaStreamSynchronize(c->copy_stream);
@@ -269,6 +284,7 @@ xg_status xg_seed(xg_ctx* ctx, uint32_t first, uint32_t count, const uint32_t* h
     if ((uint64_t)first + count > c->n) return fail(XG_EINVAL, "seed range out of bounds");
     if (count == 0) return XG_OK;
     if (!host_seeds) return fail(XG_EINVAL, "null seeds");
+    if (c->server) return fail(XG_EINVAL, "the request server owns this context; stop it first");
     std::lock_guard<std::mutex> lk(c->mu);
     uint32_t* d = nullptr;
     XG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), (size_t)count * 4, c->stream), "cudaMallocAsync(seeds)");
@@ -308,6 +324,7 @@ xg_status xg_set_state(xg_ctx* ctx, uint32_t stream, const uint32_t* ring, uint3
     Ctx* c = ctx;
     if (stream >= c->n) return fail(XG_EINVAL, "stream %u out of range", stream);
     if (!ring) return fail(XG_EINVAL, "null ring");
+    if (c->server) return fail(XG_EINVAL, "the request server owns this context; stop it first");
     std::lock_guard<std::mutex> lk(c->mu);
     uint32_t win[xg::kWin] = {0};
     std::memcpy(win + xg::kRingBase, ring, 128 * 4);
@@ -342,6 +359,7 @@ xg_status xg_generate_normal_sum(xg_ctx* ctx, uint32_t first, uint32_t nstreams,
     if (nstreams == 0) return XG_OK;
     if (!d_sums) return fail(XG_EINVAL, "null sums");
     if (!is_device_pointer(d_sums)) return fail(XG_EINVAL, "sums must be device memory");
+    if (c->server) return fail(XG_EINVAL, "the request server owns this context; use xg_submit");
     std::lock_guard<std::mutex> lk(c->mu);
     return enqueue_gen(c, xg::kNormalSum, first, nstreams, n, nullptr, 0, d_sums, c->stream);
 }

@@ -11,6 +11,10 @@
 
 namespace xg {
 class Server;
+class BatchLauncher;
+// Set the calling thread's xg_last_error() message and return st.
+xg_status fail(xg_status st, const char* fmt, ...);
+xg_status cuda_fail(cudaError_t e, const char* what);
 }
 
 struct xg_ctx {
@@ -32,6 +36,8 @@ struct xg_ctx {
     cudaEvent_t ev_copy[2] = {nullptr, nullptr};
     std::mutex mu;
     xg::Server* server = nullptr;
+    xg::BatchLauncher* batch[2] = {nullptr, nullptr};
+    int batch_next = 0;
 
     int pick_cfg(int kind, uint32_t nstreams) const;
     xg_status ensure_staging(size_t bytes);

@@ -1,4 +1,533 @@
-// Request server (continuous batching); see xg_ctx::shutdown_server.
+// Request server: continuous batching of generation requests on resident
+// streams.
+//
+//   submit  -> admission: outstanding output bytes (library pool and caller
+//              buffers) stay under the memory cap, else XG_EAGAIN; a pool
+//              buffer is carved when the caller passes no output.
+//   queue   -> per-stream FIFO; a stream has at most one request on the GPU,
+//              so its requests run in submission order.
+//   batch   -> whenever a lane (CUDA stream with its own batch launcher) is
+//              free, the oldest ready requests (one per stream) form a batch
+//              that runs as one replay of the persistent batch kernel graph.
+//              Batches on different lanes overlap on the device, so requests
+//              that arrive while others run start as soon as a lane frees.
+//   complete-> the kernel fences each request's stores and sets its flag in
+//              mapped pinned host memory; xg_poll reads it directly.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <new>
+#include <queue>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "xg_batch.h"
 #include "xg_runtime.h"
 
-void xg_ctx::shutdown_server() {}
+namespace xg {
+
+static uint64_t now_ns()
+{
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// First-fit sub-allocator over one device slab; free blocks coalesce.
+class DevicePool {
+public:
+    ~DevicePool()
+    {
+        if (base_) cudaFree(base_);
+    }
+    xg_status init(size_t cap)
+    {
+        cap_ = cap / kAlign * kAlign;
+        if (cudaMalloc(reinterpret_cast<void**>(&base_), cap_) != cudaSuccess) {
+            cudaGetLastError();
+            base_ = nullptr;
+            return fail(XG_ENOMEM, "server pool: cudaMalloc(%zu) failed", cap_);
+        }
+        free_.clear();
+        free_[0] = cap_;
+        return XG_OK;
+    }
+    void* alloc(size_t bytes)
+    {
+        bytes = (bytes + kAlign - 1) / kAlign * kAlign;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const size_t off = it->first, sz = it->second;
+                free_.erase(it);
+                if (sz > bytes) free_[off + bytes] = sz - bytes;
+                used_[off] = bytes;
+                return base_ + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(void* p)
+    {
+        const size_t off = static_cast<char*>(p) - base_;
+        auto u = used_.find(off);
+        if (u == used_.end()) return;
+        size_t sz = u->second;
+        used_.erase(u);
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + sz == next->first) {
+            sz += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += sz;
+                return;
+            }
+        }
+        free_[off] = sz;
+    }
+    size_t capacity() const { return cap_; }
+
+private:
+    static constexpr size_t kAlign = 256;
+    char* base_ = nullptr;
+    size_t cap_ = 0;
+    std::map<size_t, size_t> free_;
+    std::unordered_map<size_t, size_t> used_;
+};
+
+struct Ticket {
+    uint64_t id = 0;
+    uint64_t seq = 0;
+    xg_request req{};
+    void* out = nullptr;
+    bool pooled = false;
+    size_t bytes = 0;
+    uint32_t slot = 0;
+    std::atomic<int> state{0};  // kQueued, kRunning, kDone, kFailed
+    uint64_t t_submit = 0, t_launch = 0;
+    std::atomic<uint64_t> t_done{0};
+};
+
+enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+
+class Server {
+public:
+    explicit Server(xg_ctx* c) : c_(c) {}
+    ~Server() { stop(); }
+
+    xg_status start(const xg_server_config& cfg)
+    {
+        cfg_ = cfg;
+        if (cfg_.mem_cap_bytes == 0) cfg_.mem_cap_bytes = size_t(16) << 30;
+        if (cfg_.max_batch == 0) cfg_.max_batch = 1024;
+        if (cfg_.lanes == 0) cfg_.lanes = 16;
+        if (cfg_.lanes > 64) return fail(XG_EINVAL, "at most 64 lanes");
+        if (xg_status s = pool_.init(cfg_.mem_cap_bytes)) return s;
+        const size_t nflags = (size_t)cfg_.lanes * cfg_.max_batch;
+        if (cudaHostAlloc(reinterpret_cast<void**>(&h_flags_), nflags * 4, cudaHostAllocMapped) != cudaSuccess)
+            return fail(XG_ENOMEM, "server: pinned flag allocation failed");
+        std::memset(h_flags_, 0, nflags * 4);
+        if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_flags_), h_flags_, 0) != cudaSuccess)
+            return fail(XG_ECUDA, "server: cudaHostGetDevicePointer failed");
+        lanes_.resize(cfg_.lanes);
+        for (auto& l : lanes_) {
+            l.launcher = std::make_unique<BatchLauncher>();
+            if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(XG_ECUDA, "server: stream creation failed");
+            if (xg_status s = l.launcher->reserve(c_, cfg_.max_batch)) return fail(s, "server: batch launcher");
+        }
+        run_ = true;
+        th_ = std::thread([this] { loop(); });
+        return XG_OK;
+    }
+
+    void stop()
+    {
+        if (run_.exchange(false)) {
+            cv_.notify_all();
+            if (th_.joinable()) th_.join();
+        }
+        for (auto& l : lanes_) {
+            if (l.stream) {
+                cudaStreamSynchronize(l.stream);
+                l.launcher.reset();
+                cudaStreamDestroy(l.stream);
+                l.stream = nullptr;
+            }
+        }
+        lanes_.clear();
+        if (h_flags_) cudaFreeHost(h_flags_);
+        h_flags_ = nullptr;
+    }
+
+    xg_status submit(const xg_request& r, uint64_t* ticket)
+    {
+        if (!ticket) return fail(XG_EINVAL, "null ticket");
+        if (r.stream >= c_->n) return fail(XG_EINVAL, "stream %u out of range", r.stream);
+        if (r.type > XG_NORMAL_F32) return fail(XG_EINVAL, "unknown type %u", r.type);
+        if (r.count == 0) return fail(XG_EINVAL, "empty request");
+        if (reinterpret_cast<uintptr_t>(r.d_out) & 3u) return fail(XG_EINVAL, "output not 4-byte aligned");
+        auto t = std::make_shared<Ticket>();
+        t->req = r;
+        t->bytes = (size_t)r.count * 4;
+        std::lock_guard<std::mutex> lk(mu_);
+        if (outstanding_ + t->bytes > cfg_.mem_cap_bytes) {
+            ++refused_;
+            return fail(XG_EAGAIN, "admission refused: %zu bytes outstanding, cap %llu", outstanding_,
+                        (unsigned long long)cfg_.mem_cap_bytes);
+        }
+        if (r.d_out) {
+            t->out = r.d_out;
+        } else {
+            t->out = pool_.alloc(t->bytes);
+            if (!t->out) {
+                ++refused_;
+                return fail(XG_EAGAIN, "admission refused: no pool block of %zu bytes", t->bytes);
+            }
+            t->pooled = true;
+        }
+        outstanding_ += t->bytes;
+        t->id = next_id_++;
+        t->seq = t->id;
+        t->t_submit = now_ns();
+        tickets_[t->id] = t;
+        incoming_.push_back(t);
+        ++submitted_;
+        *ticket = t->id;
+        cv_.notify_one();
+        return XG_OK;
+    }
+
+    std::shared_ptr<Ticket> find(uint64_t id)
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = tickets_.find(id);
+        return it == tickets_.end() ? nullptr : it->second;
+    }
+
+    bool check_flag(Ticket& t)
+    {
+        const int st = t.state.load(std::memory_order_acquire);
+        if (st == kDone || st == kFailed) return true;
+        if (t.state.load(std::memory_order_acquire) != kRunning) return false;
+        volatile uint32_t* f = h_flags_ + t.slot;
+        if (*f == 0) return false;
+        int expect = kRunning;
+        if (t.state.compare_exchange_strong(expect, kDone)) t.t_done.store(now_ns());
+        return true;
+    }
+
+    xg_status poll(uint64_t id, int* done, void** out)
+    {
+        auto t = find(id);
+        if (!t) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
+        const bool d = check_flag(*t);
+        if (t->state.load() == kFailed) return fail(XG_EDEVICE, "ticket %llu failed: its batch did not run",
+                                                    (unsigned long long)id);
+        if (done) *done = d ? 1 : 0;
+        if (out) *out = d ? t->out : nullptr;
+        return XG_OK;
+    }
+
+    xg_status wait(uint64_t id, uint32_t timeout_ms, void** out)
+    {
+        auto t = find(id);
+        if (!t) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
+        const uint64_t deadline = now_ns() + (uint64_t)timeout_ms * 1000000ull;
+        while (!check_flag(*t)) {
+            if (now_ns() > deadline) return fail(XG_ETIMEDOUT, "ticket %llu not done after %u ms",
+                                                 (unsigned long long)id, timeout_ms);
+            std::this_thread::yield();
+        }
+        if (t->state.load() == kFailed) return fail(XG_EDEVICE, "ticket %llu failed: its batch did not run",
+                                                    (unsigned long long)id);
+        if (out) *out = t->out;
+        return XG_OK;
+    }
+
+    xg_status release(uint64_t id)
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = tickets_.find(id);
+        if (it == tickets_.end()) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
+        Ticket& t = *it->second;
+        if (t.state.load() != kDone && t.state.load() != kFailed) {
+            // the scheduler may not have seen the flag yet
+            volatile uint32_t* f = h_flags_ + t.slot;
+            if (!(t.state.load() == kRunning && *f)) return fail(XG_EINVAL, "ticket %llu still in flight",
+                                                                 (unsigned long long)id);
+        }
+        if (t.pooled) pool_.release(t.out);
+        outstanding_ -= t.bytes;
+        tickets_.erase(it);
+        return XG_OK;
+    }
+
+    xg_status times(uint64_t id, uint64_t* ts, uint64_t* tl, uint64_t* td)
+    {
+        auto t = find(id);
+        if (!t) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
+        check_flag(*t);
+        if (ts) *ts = t->t_submit;
+        if (tl) *tl = t->t_launch;
+        if (td) *td = t->t_done.load();
+        return XG_OK;
+    }
+
+    void stats(xg_server_stats* s)
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        s->submitted = submitted_;
+        s->completed = completed_.load();
+        s->refused = refused_;
+        s->outstanding_bytes = outstanding_;
+        s->batches = batches_.load();
+        s->items_launched = items_launched_.load();
+        s->queued = queued_.load();
+        s->in_flight = in_flight_.load();
+        s->now_ns = now_ns();
+    }
+
+private:
+    struct Lane {
+        cudaStream_t stream = nullptr;
+        std::unique_ptr<BatchLauncher> launcher;
+        std::vector<std::shared_ptr<Ticket>> inflight;
+        bool busy = false;
+    };
+
+    void loop()
+    {
+        std::vector<std::shared_ptr<Ticket>> fresh;
+        std::vector<HostItem> items;
+        while (run_.load()) {
+            bool progress = false;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                if (incoming_.empty() && !any_busy() && ready_.empty()) {
+                    cv_.wait_for(lk, std::chrono::milliseconds(2));
+                }
+                fresh.assign(incoming_.begin(), incoming_.end());
+                incoming_.clear();
+            }
+            for (auto& t : fresh) {
+                auto& q = fifo_[t->req.stream];
+                q.push_back(t);
+                if (q.size() == 1 && !busy_streams_.count(t->req.stream)) ready_.push({t->seq, t->req.stream});
+                ++queued_;
+                progress = true;
+            }
+            fresh.clear();
+            // completions
+            for (size_t li = 0; li < lanes_.size(); ++li) {
+                Lane& l = lanes_[li];
+                if (!l.busy) continue;
+                bool all = true;
+                for (auto& t : l.inflight) {
+                    if (!t) continue;
+                    if (check_flag(*t)) {
+                        finish(t);
+                        t.reset();
+                        progress = true;
+                    } else {
+                        all = false;
+                    }
+                }
+                cudaError_t e = cudaEventQuery(l.launcher->done_event());
+                if (e != cudaErrorNotReady) {
+                    // the batch is over: a request whose flag is still clear
+                    // was not run (launch or kernel error) and fails
+                    for (auto& t : l.inflight)
+                        if (t && !check_flag(*t)) fail_ticket(t);
+                    if (e != cudaSuccess) cudaGetLastError();
+                    l.busy = false;
+                    l.inflight.clear();
+                    progress = true;
+                }
+                (void)all;
+            }
+            // launches
+            for (size_t li = 0; li < lanes_.size() && !ready_.empty(); ++li) {
+                Lane& l = lanes_[li];
+                if (l.busy) continue;
+                items.clear();
+                l.inflight.clear();
+                std::memset(h_flags_ + li * cfg_.max_batch, 0, (size_t)cfg_.max_batch * 4);
+                const uint64_t t_launch = now_ns();
+                while (!ready_.empty() && items.size() < cfg_.max_batch) {
+                    const uint32_t s = ready_.top().second;
+                    ready_.pop();
+                    auto& q = fifo_[s];
+                    auto t = q.front();
+                    q.pop_front();
+                    if (q.empty()) fifo_.erase(s);
+                    busy_streams_.insert(s);
+                    t->slot = (uint32_t)(li * cfg_.max_batch + items.size());
+                    t->t_launch = t_launch;
+                    t->state.store(kRunning, std::memory_order_release);
+                    items.push_back(HostItem{s, t->req.type, t->req.count, t->out, d_flags_ + t->slot});
+                    l.inflight.push_back(t);
+                    --queued_;
+                }
+                if (items.empty()) continue;
+                in_flight_ += items.size();
+                if (l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream) != XG_OK) {
+                    cudaGetLastError();
+                    launch_error_ = true;
+                    for (auto& t : l.inflight) fail_ticket(t);
+                    l.inflight.clear();
+                    continue;
+                }
+                l.busy = true;
+                ++batches_;
+                items_launched_ += items.size();
+                progress = true;
+            }
+            if (!progress) std::this_thread::yield();
+        }
+    }
+
+    bool any_busy() const
+    {
+        for (auto& l : lanes_)
+            if (l.busy) return true;
+        return false;
+    }
+
+    void fail_ticket(const std::shared_ptr<Ticket>& t)
+    {
+        int expect = kRunning;
+        if (t->state.compare_exchange_strong(expect, kFailed)) t->t_done.store(now_ns());
+        finish(t);
+    }
+
+    void finish(const std::shared_ptr<Ticket>& t)
+    {
+        const uint32_t s = t->req.stream;
+        busy_streams_.erase(s);
+        auto it = fifo_.find(s);
+        if (it != fifo_.end() && !it->second.empty()) ready_.push({it->second.front()->seq, s});
+        ++completed_;
+        --in_flight_;
+    }
+
+    xg_ctx* c_;
+    xg_server_config cfg_{};
+    DevicePool pool_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::unordered_map<uint64_t, std::shared_ptr<Ticket>> tickets_;
+    std::deque<std::shared_ptr<Ticket>> incoming_;
+    uint64_t next_id_ = 1;
+    size_t outstanding_ = 0;
+    uint64_t submitted_ = 0, refused_ = 0;
+    std::atomic<uint64_t> completed_{0}, batches_{0}, items_launched_{0}, queued_{0}, in_flight_{0};
+    std::atomic<bool> launch_error_{false};
+    // scheduler thread only
+    std::unordered_map<uint32_t, std::deque<std::shared_ptr<Ticket>>> fifo_;
+    std::unordered_set<uint32_t> busy_streams_;
+    std::priority_queue<std::pair<uint64_t, uint32_t>, std::vector<std::pair<uint64_t, uint32_t>>,
+                        std::greater<std::pair<uint64_t, uint32_t>>>
+        ready_;
+    std::vector<Lane> lanes_;
+    uint32_t* h_flags_ = nullptr;
+    uint32_t* d_flags_ = nullptr;
+    std::thread th_;
+    std::atomic<bool> run_{false};
+
+    friend void ::xg_ctx::shutdown_server();
+};
+
+}  // namespace xg
+
+void xg_ctx::shutdown_server()
+{
+    if (server) {
+        server->stop();
+        delete server;
+        server = nullptr;
+    }
+}
+
+using xg::fail;
+
+extern "C" {
+
+xg_status xg_server_start(xg_ctx* ctx, const xg_server_config* cfg)
+{
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if (ctx->server) return fail(XG_EINVAL, "server already running");
+    xg_server_config c{};
+    if (cfg) c = *cfg;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStreamSynchronize(ctx->stream);
+    auto* s = new (std::nothrow) xg::Server(ctx);
+    if (!s) return fail(XG_ENOMEM, "host allocation failed");
+    if (xg_status st = s->start(c)) {
+        delete s;
+        return st;
+    }
+    ctx->server = s;
+    return XG_OK;
+}
+
+xg_status xg_server_stop(xg_ctx* ctx)
+{
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    ctx->shutdown_server();
+    return XG_OK;
+}
+
+xg_status xg_submit(xg_ctx* ctx, const xg_request* req, uint64_t* ticket)
+{
+    if (!ctx || !req) return fail(XG_EINVAL, "null argument");
+    if (!ctx->server) return fail(XG_EINVAL, "server not running (xg_server_start)");
+    return ctx->server->submit(*req, ticket);
+}
+
+xg_status xg_poll(xg_ctx* ctx, uint64_t ticket, int* done, void** d_result)
+{
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if (!ctx->server) return fail(XG_EINVAL, "server not running");
+    return ctx->server->poll(ticket, done, d_result);
+}
+
+xg_status xg_wait(xg_ctx* ctx, uint64_t ticket, uint32_t timeout_ms, void** d_result)
+{
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if (!ctx->server) return fail(XG_EINVAL, "server not running");
+    return ctx->server->wait(ticket, timeout_ms, d_result);
+}
+
+xg_status xg_release(xg_ctx* ctx, uint64_t ticket)
+{
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if (!ctx->server) return fail(XG_EINVAL, "server not running");
+    return ctx->server->release(ticket);
+}
+
+xg_status xg_ticket_times(xg_ctx* ctx, uint64_t ticket, uint64_t* t_submit_ns, uint64_t* t_launch_ns,
+                          uint64_t* t_done_ns)
+{
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if (!ctx->server) return fail(XG_EINVAL, "server not running");
+    return ctx->server->times(ticket, t_submit_ns, t_launch_ns, t_done_ns);
+}
+
+xg_status xg_server_stats_get(xg_ctx* ctx, xg_server_stats* out)
+{
+    if (!ctx || !out) return fail(XG_EINVAL, "null argument");
+    if (!ctx->server) return fail(XG_EINVAL, "server not running");
+    ctx->server->stats(out);
+    return XG_OK;
+}
+
+}  // extern "C"

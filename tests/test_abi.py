@@ -35,7 +35,7 @@ def libpath():
 def test_header_declares_the_boundary():
     names = _declared()
     for required in ("xg_create_streams", "xg_seed", "xg_generate_u32", "xg_generate_uniform",
-                     "xg_generate_normal"):
+                     "xg_generate_normal", "xg_submit", "xg_poll"):
         assert required in names, required
 
 

@@ -1,0 +1,237 @@
+"""Batched persistent kernel and request server against the oracle and
+against the plain one-launch-per-call path."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1108_0486_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KINDS = ["u32", "uniform", "normal"]
+TOL = 4.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def Streams(*a, **k):
+    from paper_1108_0486_gb300 import Streams as S
+    return S(*a, **k)
+
+
+def nwords(kind, n):
+    return n + (n & 1) if kind == "normal" else n
+
+
+def oracle_call(words, kind, n):
+    if kind == "u32":
+        return words[:n]
+    if kind == "uniform":
+        return O.uniform_of(words[:n])
+    return O.normal_pairs64(words[:nwords(kind, n)])[:n]
+
+
+def check(kind, got_tensor, ref):
+    if kind == "u32":
+        assert np.array_equal(got_tensor.cpu().numpy().view(np.uint32), ref)
+    elif kind == "uniform":
+        assert np.array_equal(got_tensor.cpu().numpy(), ref)
+    else:
+        z = got_tensor.cpu().numpy().astype(np.float64)
+        z32 = ref.astype(np.float32)
+        err = np.abs(z - ref) / np.spacing(np.abs(z32)).astype(np.float64)
+        assert float(err.max()) <= TOL, err.max()
+
+
+def alloc(kind, n):
+    return torch.empty(max(n, 1), dtype=torch.int32 if kind == "u32" else torch.float32, device="cuda")
+
+
+def random_items(rng, n_streams, n_items, max_len=40000):
+    items = []
+    for _ in range(n_items):
+        s = int(rng.integers(0, n_streams))
+        k = KINDS[int(rng.integers(0, 3))]
+        n = int(np.exp(rng.uniform(0, np.log(max_len))))
+        items.append((s, k, n))
+    return items
+
+
+def oracle_per_item(seeds, items, ps=0):
+    """The oracle outputs of each item, streams advancing in item order."""
+    total = {}
+    for s, k, n in items:
+        total[s] = total.get(s, 0) + nwords(k, n)
+    words = {s: O.Xorgens.param_set(ps).seed(int(seeds[s])).u32(t) for s, t in total.items()}
+    off = {s: 0 for s in total}
+    refs = []
+    for s, k, n in items:
+        w = words[s][off[s]:off[s] + nwords(k, n)]
+        off[s] += nwords(k, n)
+        refs.append(oracle_call(w, k, n))
+    return refs
+
+
+# ----------------------------------------------------------------- batch
+
+@pytest.mark.parametrize("ps", [0, 1])
+def test_batch_mixed_types_uneven_lengths_and_chains(ps):
+    rng = np.random.default_rng(21 + ps)
+    seeds = W.seeds(150, start=500)
+    items = random_items(rng, 150, 400)  # many streams appear several times
+    outs = [alloc(k, n) for _, k, n in items]
+    with Streams(150, param_set=ps, seeds=seeds) as st:
+        st.batch([(s, k, n, o) for (s, k, n), o in zip(items, outs)])
+        torch.cuda.synchronize()
+    for (s, k, n), o, ref in zip(items, outs, oracle_per_item(seeds, items, ps)):
+        check(k, o[:n], ref)
+
+
+def test_batch_equals_plain_calls_bitwise():
+    rng = np.random.default_rng(5)
+    seeds = W.seeds(64)
+    items = random_items(rng, 64, 200)
+    outs = [alloc(k, n) for _, k, n in items]
+    with Streams(64, seeds=seeds) as a, Streams(64, seeds=seeds) as b:
+        a.batch([(s, k, n, o) for (s, k, n), o in zip(items, outs)])
+        for (s, k, n), o in zip(items, outs):
+            ref = b.generate(k, n, first=s, count=1)[0, :n]
+            assert torch.equal(o[:n], ref)
+        # both contexts end in the same state
+        assert torch.equal(a.u32(100), b.u32(100))
+
+
+def test_batch_unaligned_outputs_and_zero_counts():
+    seeds = W.seeds(10)
+    items = [(0, "u32", 1001), (1, "uniform", 77), (2, "normal", 33), (3, "u32", 0), (0, "u32", 5)]
+    big = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    outs = [big[1:1002], big[1100:1177].view(torch.float32), big[1201:1234].view(torch.float32),
+            None, big[3001:3006]]
+    with Streams(10, seeds=seeds) as st:
+        st.batch([(s, k, n, o) for (s, k, n), o in zip(items, outs)])
+        torch.cuda.synchronize()
+    refs = oracle_per_item(seeds, items)
+    for (s, k, n), o, ref in zip(items, outs, refs):
+        if n:
+            check(k, o[:n], ref)
+
+
+def test_batch_uneven_workload_sampled():
+    """4096 streams, one item each, lengths log-uniform in [2^10, 2^24],
+    mixed types (about 29 GB of outputs), in one launch; sampled items
+    (the longest, the shortest and a few others) against the oracle."""
+    items = W.batched_uneven()
+    seeds = W.seeds(len(items))
+    outs = [alloc(KINDS[it.kind], it.count) for it in items]
+    with Streams(len(items), seeds=seeds) as st:
+        st.batch([(it.stream, it.kind, it.count, o) for it, o in zip(items, outs)])
+        torch.cuda.synchronize()
+    counts = np.array([it.count for it in items])
+    pick = list(np.argsort(counts)[[0, 1, len(items) // 2, -2, -1]]) + [7, 1234, 4095]
+    for i in pick:
+        it = items[i]
+        k = KINDS[it.kind]
+        words = O.Xorgens.param_set(0).seed(int(seeds[it.stream])).u32(nwords(k, it.count))
+        check(k, outs[i][:it.count], oracle_call(words, k, it.count))
+
+
+# ---------------------------------------------------------------- server
+
+def test_server_results_same_alone_and_in_the_mix():
+    """Requests from 4 client threads, arriving while others run; each
+    result equals the same request run alone through the plain path."""
+    rng = np.random.default_rng(9)
+    S = 300
+    seeds = W.seeds(S, start=77)
+    reqs = random_items(rng, S, 600, max_len=200000)
+    outs = [alloc(k, n) for _, k, n in reqs]
+    tickets = [None] * len(reqs)
+    with Streams(S, seeds=seeds) as st:
+        srv = st.serve(lanes=8, max_batch=64)
+
+        def client(idx):
+            for i in idx:
+                s, k, n = reqs[i]
+                tickets[i] = srv.submit(s, k, n, out=outs[i])
+
+        parts = np.array_split(np.arange(len(reqs)), 4)
+        th = [threading.Thread(target=client, args=(p,)) for p in parts]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for t in tickets:
+            srv.wait(t, 60000)
+        stats = srv.stats()
+        for t in tickets:
+            srv.release(t)
+        srv.stop()
+    assert stats["completed"] == len(reqs) and stats["batches"] >= 2
+    # per stream, submission order is ticket order
+    order = np.argsort(np.array(tickets))
+    with Streams(S, seeds=seeds) as alone:
+        for i in order:
+            s, k, n = reqs[i]
+            ref = alone.generate(k, n, first=s, count=1)[0, :n]
+            assert torch.equal(outs[i][:n], ref), (i, s, k, n)
+    # and against the oracle for a sample
+    ordered = [reqs[i] for i in order]
+    refs = oracle_per_item(seeds, ordered)
+    for j in range(0, len(ordered), 37):
+        s, k, n = ordered[j]
+        check(k, outs[order[j]][:n], refs[j])
+
+
+def test_server_pool_buffers_and_release():
+    seeds = W.seeds(20)
+    reqs = [(i % 20, KINDS[i % 3], 1000 + 37 * i) for i in range(60)]
+    with Streams(20, seeds=seeds) as st:
+        srv = st.serve(mem_cap_bytes=64 << 20)
+        tickets = [srv.submit(s, k, n) for s, k, n in reqs]
+        results = [srv.result(t, k, n).clone() for t, (_, k, n) in zip(tickets, reqs)]
+        assert srv.stats()["outstanding_bytes"] == sum(4 * n for _, _, n in reqs)
+        for t in tickets:
+            srv.release(t)
+        assert srv.stats()["outstanding_bytes"] == 0
+        srv.stop()
+    refs = oracle_per_item(seeds, reqs)
+    for (s, k, n), r, ref in zip(reqs, results, refs):
+        check(k, r[:n], ref)
+
+
+def test_server_admission_by_memory():
+    from paper_1108_0486_gb300 import XGError, _lib as L
+    with Streams(8, seeds=W.seeds(8)) as st:
+        srv = st.serve(mem_cap_bytes=1 << 20)  # 1 MiB: 262144 outputs
+        t1 = srv.submit(0, "u32", 200000)
+        with pytest.raises(XGError) as e:
+            srv.submit(1, "u32", 100000)
+        assert e.value.status == L.XG_EAGAIN
+        srv.wait(t1)
+        srv.release(t1)
+        t2 = srv.submit(1, "u32", 100000)
+        srv.wait(t2)
+        assert srv.stats()["refused"] == 1
+        srv.release(t2)
+        srv.stop()
+
+
+def test_server_owns_the_context_while_running():
+    from paper_1108_0486_gb300 import XGError, _lib as L
+    with Streams(4, seeds=W.seeds(4)) as st:
+        srv = st.serve()
+        with pytest.raises(XGError):
+            st.u32(10)
+        with pytest.raises(XGError) as e:
+            srv.poll(123456)
+        assert e.value.status == L.XG_ENOTFOUND
+        srv.stop()
+        st.u32(10)  # plain calls work again
