@@ -287,6 +287,8 @@ def run_ours(args):
     rows = {}
     if not args.quick:
         rows = extra_rows(st, stream, torch, peak)
+        rows["batched"] = batched_row(torch, L, stream, peak)
+        rows["serving"] = serving_row(torch, L, stream, seconds=args.serve_seconds)
     e2e = None
     if not args.no_e2e:
         e2e = end_to_end(st, stream, torch, L, args)
@@ -342,6 +344,137 @@ def extra_rows(st, stream, torch, peak):
     return rows
 
 
+def batched_row(torch, L, stream, peak, reps=3):
+    """4096 streams, one item each, lengths log-uniform in [2^10, 2^24],
+    types uniform over u32/uniform/normal: one persistent-kernel launch per
+    repetition (graph replay).  Also the longest item alone, which bounds the
+    launch from below (one stream is a serial chain)."""
+    from paper_1108_0486_gb300 import Streams
+    items = W.batched_uneven()
+    seeds = W.seeds(len(items))
+    total = sum(it.count for it in items)
+    outs = [torch.empty(it.count, dtype=torch.int32 if it.kind == 0 else torch.float32, device="cuda")
+            for it in items]
+    st = Streams(len(items), seeds=seeds, stream=stream)
+    spec = [(it.stream, it.kind, it.count, o.data_ptr()) for it, o in zip(items, outs)]
+    ms = _time(lambda: L.xg_generate_batch(st.ctx, spec), stream, torch, reps=reps, warm=1)
+    longest = max(range(len(items)), key=lambda i: items[i].count)
+    one = [spec[longest]]
+    ms_long = _time(lambda: L.xg_generate_batch(st.ctx, one), stream, torch, reps=reps, warm=1)
+    st.close()
+    del outs
+    torch.cuda.empty_cache()
+    return {"workload": "4096 items (streams 0..4095, seeds 1..4096), lengths log-uniform [2^10, 2^24] "
+                        "(PCG64 seed 1108), types uniform over u32/uniform/normal, one graph-replayed launch",
+            "rns_total": total, "ms": ms, "rn_s": total / (ms / 1e3),
+            "hbm_frac": total * 4 / (ms / 1e3) / 1e9 / peak,
+            "longest_item": items[longest].count, "longest_item_alone_ms": ms_long,
+            "hbm_floor_ms": total * 4 / peak / 1e6}
+
+
+def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0):
+    """Open-loop Poisson arrivals at `rate` req/s on 65536 resident streams,
+    sizes log-uniform in [2^10, 2^22], 60/30/10 normal/uniform/u32, memory
+    cap 16 GiB (library pool).  Latency = completion seen by the host minus
+    submission.  Then the plain path: one xg_generate_* launch per request on
+    one CUDA stream, same arrivals, latency from CUDA events."""
+    import threading as th
+    from paper_1108_0486_gb300 import Streams
+    S = 65536
+    reqs = W.serving_requests(n_streams=S, rate=rate, duration=seconds)
+    st = Streams(S, seeds=W.seeds(S), stream=stream)
+    torch.cuda.synchronize()
+    L.xg_server_start(st.ctx, 16 << 30, 1024, 16)
+    tickets = []
+    lock = th.Lock()
+    done_times = []
+    refused = [0]
+    stop = [False]
+
+    def reaper():
+        pending = []
+        while True:
+            with lock:
+                pending.extend(tickets)
+                tickets.clear()
+            still = []
+            for t in pending:
+                done, _ = L.xg_poll(st.ctx, t)
+                if done:
+                    done_times.append(L.xg_ticket_times(st.ctx, t))
+                    L.xg_release(st.ctx, t)
+                else:
+                    still.append(t)
+            pending = still
+            if stop[0] and not pending:
+                with lock:
+                    if not tickets:
+                        return
+            time.sleep(0.0002)
+
+    rt = th.Thread(target=reaper)
+    rt.start()
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r.t_arrival:
+            pass
+        while True:
+            try:
+                t = L.xg_submit(st.ctx, r.stream, r.kind, r.count, 0)
+                break
+            except L.XGError as e:
+                if e.status != L.XG_EAGAIN:
+                    raise
+                refused[0] += 1
+                time.sleep(0.0001)
+        with lock:
+            tickets.append(t)
+    stop[0] = True
+    rt.join()
+    wall = time.perf_counter() - t0
+    stats = L.xg_server_stats_get(st.ctx)
+    L.xg_server_stop(st.ctx)
+    lat = np.array([(d - s) / 1e6 for s, _, d in done_times])
+    qwait = np.array([(l - s) / 1e6 for s, l, _ in done_times])
+    words = sum(r.count for r in reqs)
+    span = (max(d for _, _, d in done_times) - min(s for s, _, _ in done_times)) / 1e9
+    row = {"workload": f"65536 streams, Poisson {rate:.0f} req/s for {seconds:g} s, sizes log-uniform "
+                       "[2^10, 2^22], 60/30/10 normal/uniform/u32 (PCG64 seed 486), cap 16 GiB",
+           "requests": len(reqs), "rns": words, "rn_s": words / span, "offered_rn_s": words / seconds,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "max_ms": float(lat.max()), "p50_queue_ms": float(np.percentile(qwait, 50)),
+           "p99_queue_ms": float(np.percentile(qwait, 99)), "refused_retries": refused[0],
+           "batches": stats["batches"], "mean_batch": stats["items_launched"] / max(1, stats["batches"]),
+           "wall_s": wall}
+    # plain path: one launch per request, in arrival order, on one CUDA stream
+    preqs = [r for r in reqs if r.t_arrival < plain_seconds]
+    buf = torch.empty(1 << 22, dtype=torch.int32, device="cuda")
+    fns = [L.xg_generate_u32, L.xg_generate_uniform, L.xg_generate_normal]
+    evs = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    t0 = time.perf_counter()
+    arrivals = []
+    for r in preqs:
+        while time.perf_counter() - t0 < r.t_arrival:
+            pass
+        arrivals.append(time.perf_counter() - t0)
+        fns[r.kind](st.ctx, r.stream, 1, r.count, buf.data_ptr(), r.count)
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        evs.append(e)
+    torch.cuda.synchronize()
+    plat = np.array([e0.elapsed_time(e) / 1e3 - a for e, a in zip(evs, arrivals)]) * 1e3
+    row["plain_one_launch_per_request"] = {
+        "requests": len(preqs), "window_s": plain_seconds,
+        "p50_ms": float(np.percentile(plat, 50)), "p99_ms": float(np.percentile(plat, 99)),
+        "max_ms": float(plat.max()),
+        "note": "same arrivals; a single CUDA stream serialises the launches, so the queue grows"}
+    st.close()
+    return row
+
+
 def end_to_end(st, stream, torch, L, args):
     """The same step through the C ABI into pinned host memory: each call
     generates on the device in pieces and copies them to the host while the
@@ -376,6 +509,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the extra rows")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="arrival window of the serving row (10 s for the full 200K requests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-per", type=int, default=None,
                     help="override words per stream (profiling of a smaller case; not a bench line)")

@@ -343,10 +343,14 @@ private:
                 }
                 cudaError_t e = cudaEventQuery(l.launcher->done_event());
                 if (e != cudaErrorNotReady) {
-                    // the batch is over: a request whose flag is still clear
-                    // was not run (launch or kernel error) and fails
-                    for (auto& t : l.inflight)
-                        if (t && !check_flag(*t)) fail_ticket(t);
+                    // the batch is over: every request left is resolved now,
+                    // finished if its flag has become visible meanwhile,
+                    // failed (not run: launch or kernel error) otherwise
+                    for (auto& t : l.inflight) {
+                        if (!t) continue;
+                        if (check_flag(*t)) finish(t);
+                        else fail_ticket(t);
+                    }
                     if (e != cudaSuccess) cudaGetLastError();
                     l.busy = false;
                     l.inflight.clear();
