@@ -156,6 +156,28 @@ typedef struct {
  * generator with its own state. */
 xg_status xg_generate_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items);
 
+/* The same batched generation for callers that must not allocate memory
+ * while they run -- for example an application whose device memory is owned
+ * by another allocator, or a latency-critical loop that cannot take
+ * cudaMalloc's implicit device synchronisation.  (The paper has no
+ * counterpart: this is a property of the library, not of the method.)
+ * Calls no cudaMalloc, cudaFree or other allocating routine: the batch
+ * description goes to a fixed device array inside the library (about 44 KiB,
+ * held by every GPU that loads the library until the process exits) with one
+ * cudaMemcpyAsync from a buffer on the calling thread's stack, and the
+ * persistent batch kernel of xg_generate_batch runs on it.  Results are
+ * identical to xg_generate_batch's.
+ *   - At most 1024 items per call; more is XG_EINVAL.
+ *   - The context's device must be current.  The first call on a device looks
+ *     up the array's device address (once per device); make that first call
+ *     before any stream capture.
+ *   - The array is shared by every call and keeps the last call's batch; each
+ *     call rewrites its header, including the work counter that starts at
+ *     zero.  Calls whose kernels overlap on the GPU (different CUDA streams,
+ *     other contexts on the same device, other threads) race on the array:
+ *     order them on one stream or synchronise between them. */
+xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items, uint32_t n_items);
+
 /* ---- serving: continuous batching of requests --------------------------- */
 
 typedef struct {

@@ -69,6 +69,7 @@ SIGNATURES = {
     "xg_transform_uniform": [vp, vp, u64, vp],
     "xg_transform_normal": [vp, vp, u64, vp],
     "xg_generate_batch": [vp, vp, u32],
+    "xg_generate_batch_noalloc": [vp, vp, u32],
     "xg_server_start": [vp, vp],
     "xg_server_stop": [vp],
     "xg_submit": [vp, vp, P_u64],
@@ -181,6 +182,12 @@ def xg_generate_batch(ctx, items) -> None:
     """items: sequence of (stream, type, count, out_ptr)."""
     arr = (XgItem * len(items))(*[XgItem(s, t, c, o) for s, t, c, o in items])
     call("xg_generate_batch", ctypes.c_void_p(ctx), arr, len(items))
+
+
+def xg_generate_batch_noalloc(ctx, items) -> None:
+    """items: sequence of (stream, type, count, out_ptr); at most 1024."""
+    arr = (XgItem * len(items))(*[XgItem(s, t, c, o) for s, t, c, o in items])
+    call("xg_generate_batch_noalloc", ctypes.c_void_p(ctx), arr, len(items))
 
 
 def xg_server_start(ctx, mem_cap_bytes=0, max_batch=0, lanes=0) -> None:
