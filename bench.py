@@ -230,6 +230,10 @@ def run_ours(args):
     buf_u = torch.empty((STREAMS, N_PER), dtype=torch.int32, device="cuda")
     buf_f = torch.empty((STREAMS, N_PER), dtype=torch.float32, device="cuda")
     launches_per_step = 2
+    tuned = {}
+    if not args.no_autotune:
+        for kind in ("u32", "uniform", "normal"):
+            tuned[kind] = st.autotune(kind, N_PER)
 
     ev = []  # (start, mid, end) events per step: u32 kernel, uniform kernel
 
@@ -299,7 +303,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": dict(CONFIG, parallelism=f"independent streams x{ws}"),
+                "config": dict(CONFIG, parallelism=f"independent streams x{ws}", launch=tuned),
                 "roofline": roofline, "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk, "e2e": e2e, "rows": rows}
         if not args.no_cpu_baseline and ws == 1:
@@ -509,6 +513,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the extra rows")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="arrival window of the serving row (10 s for the full 200K requests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

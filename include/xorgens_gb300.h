@@ -250,6 +250,15 @@ xg_status xg_server_stats_get(xg_ctx* ctx, xg_server_stats* out);
 xg_status xg_set_launch(xg_ctx* ctx, xg_type type, uint32_t tpg, uint32_t wpl);
 xg_status xg_get_launch(const xg_ctx* ctx, xg_type type, uint32_t* tpg, uint32_t* wpl);
 
+/* Autotuner: time every supported (tpg, wpl) with 32, 64, 128 and 256
+ * threads per block on a slice of the workload (nstreams streams -- 0 = all
+ * -- by up to n_per_stream outputs, at most 2^27 outputs in all), keep the
+ * fastest for later calls of this type and return it (outputs may be NULL).
+ * The streams do not advance: their state is saved and restored around the
+ * timing runs.  Synchronous; allocates a temporary buffer for the slice. */
+xg_status xg_autotune(xg_ctx* ctx, xg_type type, uint32_t nstreams, uint64_t n_per_stream,
+                      uint32_t* tpg, uint32_t* wpl, uint32_t* block, float* best_ms);
+
 /* ---- errors ------------------------------------------------------------- */
 
 /* Thread-local description of the last failure on this thread ("" if none). */

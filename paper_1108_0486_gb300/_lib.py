@@ -80,6 +80,7 @@ SIGNATURES = {
     "xg_server_stats_get": [vp, vp],
     "xg_set_launch": [vp, i32, u32, u32],
     "xg_get_launch": [vp, i32, P_u32, P_u32],
+    "xg_autotune": [vp, i32, u32, u64, P_u32, P_u32, P_u32, ctypes.POINTER(ctypes.c_float)],
     "xg_last_error": [],
     "xg_version": [],
 }
@@ -242,6 +243,13 @@ def xg_get_launch(ctx, out_type):
     t, w = ctypes.c_uint32(), ctypes.c_uint32()
     call("xg_get_launch", ctypes.c_void_p(ctx), out_type, ctypes.byref(t), ctypes.byref(w))
     return t.value, w.value
+
+
+def xg_autotune(ctx, out_type, nstreams, n_per_stream):
+    t, w, b, ms = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_float()
+    call("xg_autotune", ctypes.c_void_p(ctx), out_type, nstreams, n_per_stream, ctypes.byref(t),
+         ctypes.byref(w), ctypes.byref(b), ctypes.byref(ms))
+    return {"tpg": t.value, "wpl": w.value, "block": b.value, "ms": ms.value}
 
 
 def xg_version() -> str:

@@ -78,6 +78,10 @@ class Streams:
     def get_launch(self, kind: str):
         return L.xg_get_launch(self.ctx, TYPES[kind])
 
+    def autotune(self, kind: str, n_per_stream: int, nstreams: int = 0) -> dict:
+        """Pick the fastest launch for this type on this workload shape."""
+        return L.xg_autotune(self.ctx, TYPES[kind], nstreams, n_per_stream)
+
     # ---- generation -----------------------------------------------------
     def _gen(self, fn, dtype, n, first, count, out, ld):
         count = self.n - first if count is None else count

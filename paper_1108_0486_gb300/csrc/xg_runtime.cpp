@@ -69,6 +69,12 @@ int xg_ctx::pick_cfg(int kind, uint32_t nstreams) const
     return xg::cfg_index(32, 2);
 }
 
+int xg_ctx::pick_block(int kind, int c) const
+{
+    const int t = kind == xg::kNormalSum ? xg::kNormal : kind;
+    return (cfg[t] == c && blk[t] > 0) ? blk[t] : block[c];
+}
+
 xg_status xg_ctx::ensure_staging(size_t bytes)
 {
     if (staging_bytes >= bytes) return XG_OK;
@@ -91,7 +97,8 @@ static xg_status check_ctx(const xg_ctx* c)
 }
 
 static xg_status enqueue_gen(Ctx* c, int kind, uint32_t first, uint32_t nstreams, uint64_t n,
-                             void* d_out, uint64_t ld, float* d_sums, cudaStream_t s)
+                             void* d_out, uint64_t ld, float* d_sums, cudaStream_t s,
+                             int force_cfg = -1, int force_block = 0)
 {
     xg::GenArgs a{};
     a.st = c->st;
@@ -102,10 +109,10 @@ static xg_status enqueue_gen(Ctx* c, int kind, uint32_t first, uint32_t nstreams
     a.ld = ld;
     a.sums = d_sums;
     a.omega = c->weyl_on ? kOmegaHost : 0u;
-    const int cfg = c->pick_cfg(kind, nstreams);
+    const int cfg = force_cfg >= 0 ? force_cfg : c->pick_cfg(kind, nstreams);
     const bool vec = kind == xg::kNormalSum ||
                      (((reinterpret_cast<uintptr_t>(d_out) & 15u) == 0) && (ld % 4 == 0));
-    const int block = c->block[cfg];
+    const int block = force_block > 0 ? force_block : c->pick_block(kind, cfg);
     cudaError_t e = xg::launch_gen(c->param_set, cfg, kind, vec, block, a, s);
     if (e != cudaSuccess) return cuda_fail(e, "generate kernel launch");
     return XG_OK;
@@ -391,6 +398,7 @@ xg_status xg_set_launch(xg_ctx* ctx, xg_type type, uint32_t tpg, uint32_t wpl)
 {
     if (xg_status s = check_ctx(ctx)) return s;
     if ((unsigned)type > XG_NORMAL_F32) return fail(XG_EINVAL, "unknown output type");
+    ctx->blk[type] = 0;
     if (tpg == 0 && wpl == 0) {
         ctx->cfg[type] = -1;
         return XG_OK;
@@ -413,6 +421,80 @@ xg_status xg_get_launch(const xg_ctx* ctx, xg_type type, uint32_t* tpg, uint32_t
         *tpg = (uint32_t)xg::kCfgs[ci].tpg;
         *wpl = (uint32_t)xg::kCfgs[ci].wpl;
     }
+    return XG_OK;
+}
+
+xg_status xg_autotune(xg_ctx* ctx, xg_type type, uint32_t nstreams, uint64_t n_per_stream,
+                      uint32_t* tpg, uint32_t* wpl, uint32_t* block, float* best_ms)
+{
+    if (xg_status s = check_ctx(ctx)) return s;
+    Ctx* c = ctx;
+    if ((unsigned)type > XG_NORMAL_F32) return fail(XG_EINVAL, "unknown output type");
+    if (c->server) return fail(XG_EINVAL, "the request server owns this context; stop it first");
+    if (nstreams == 0 || nstreams > c->n) nstreams = c->n;
+    if (n_per_stream == 0) return fail(XG_EINVAL, "n_per_stream must be positive");
+    // a slice of the workload: every stream, at most 2^27 outputs in all
+    uint64_t nt = std::min<uint64_t>(n_per_stream, std::max<uint64_t>(256, (uint64_t(1) << 27) / nstreams));
+    nt = align_up(nt, 64);
+    std::lock_guard<std::mutex> lk(c->mu);
+    const size_t state_bytes = (size_t)((char*)(c->st.pos + c->n) - (char*)c->state_mem);
+    void* saved = nullptr;
+    void* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    xg_status st = XG_OK;
+    int best_cfg = -1, best_block = 0;
+    float best = 1e30f;
+    auto cleanup = [&]() {
+        if (saved) {
+            cudaMemcpyAsync(c->state_mem, saved, state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+            cudaStreamSynchronize(c->stream);
+            cudaFree(saved);
+        }
+        if (out) cudaFree(out);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&saved, state_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(saved, c->state_mem, state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)nstreams * nt * 4);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return cuda_fail(e, "autotune set-up");
+    }
+    static const int kBlocks[] = {32, 64, 128, 256};
+    for (int ci = 0; ci < xg::kNumCfgs && st == XG_OK; ++ci) {
+        for (int b : kBlocks) {
+            st = enqueue_gen(c, type, 0, nstreams, nt, out, nt, nullptr, c->stream, ci, b);
+            if (st != XG_OK) break;
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 3 && st == XG_OK; ++r)
+                st = enqueue_gen(c, type, 0, nstreams, nt, out, nt, nullptr, c->stream, ci, b);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = cuda_fail(cudaGetLastError(), "autotune timing");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3.f;
+            if (ms < best) {
+                best = ms;
+                best_cfg = ci;
+                best_block = b;
+            }
+        }
+    }
+    cleanup();
+    if (st != XG_OK) return st;
+    c->cfg[type] = best_cfg;
+    c->blk[type] = best_block;
+    if (tpg) *tpg = (uint32_t)xg::kCfgs[best_cfg].tpg;
+    if (wpl) *wpl = (uint32_t)xg::kCfgs[best_cfg].wpl;
+    if (block) *block = (uint32_t)best_block;
+    if (best_ms) *best_ms = best;
     return XG_OK;
 }
 

@@ -27,6 +27,7 @@ struct xg_ctx {
     void* state_mem = nullptr;
     xg::State st{};
     int cfg[3] = {-1, -1, -1};      // per output type; -1 = automatic
+    int blk[3] = {0, 0, 0};         // tuned threads per block per output type; 0 = the cfg's default
     int block[xg::kNumCfgs] = {};   // threads per block per configuration
     // host-output staging
     void* staging[2] = {nullptr, nullptr};
@@ -40,6 +41,7 @@ struct xg_ctx {
     int batch_next = 0;
 
     int pick_cfg(int kind, uint32_t nstreams) const;
+    int pick_block(int kind, int cfg) const;
     xg_status ensure_staging(size_t bytes);
     void shutdown_server();
 };

@@ -235,3 +235,20 @@ def test_server_owns_the_context_while_running():
         assert e.value.status == L.XG_ENOTFOUND
         srv.stop()
         st.u32(10)  # plain calls work again
+
+
+# -------------------------------------------------------------- autotuner
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_autotune_picks_a_supported_launch_and_leaves_streams_in_place(kind):
+    from paper_1108_0486_gb300.api import LAUNCHES
+    seeds = W.seeds(2000, start=3)
+    with Streams(2000, seeds=seeds) as st:
+        st.u32(77)  # a position that is not a multiple of the round width
+        best = st.autotune(kind, 4096)
+        assert (best["tpg"], best["wpl"]) in LAUNCHES and best["block"] in (32, 64, 128, 256)
+        assert st.get_launch(kind) == (best["tpg"], best["wpl"])
+        got = st.generate(kind, 3001)
+    ref = O.streams(seeds, 77 + nwords(kind, 3001))[:, 77:]
+    for i in (0, 999, 1999):
+        check(kind, got[i, :3001], oracle_call(ref[i], kind, 3001))
