@@ -178,6 +178,27 @@ xg_status xg_generate_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items)
  *     order them on one stream or synchronise between them. */
 xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items, uint32_t n_items);
 
+/* Cutting long calls in batches: a call that is alone on its stream in a
+ * batch (xg_generate_batch and the request server) and has at least twice
+ * piece_words words is cut into pieces of piece_words words that different
+ * warps generate at once; each piece starts from the stream's state jumped
+ * ahead by its offset (see xg_jump), so the output is exactly that of the
+ * uncut call.  piece_words: 0 = automatic (about the batch's words per
+ * resident warp, between 2^16 and 2^22), 1 = never cut, else a power of two
+ * >= 64. */
+xg_status xg_set_batch_split(xg_ctx* ctx, uint64_t piece_words);
+
+/* Jump-ahead: advance streams [first, first+nstreams) by `words` positions
+ * without generating them, exactly as if that many words had been drawn
+ * (the recurrence of Sec. 2 is linear over GF(2) on the 4096-bit ring, so
+ * the jump is a product of precomputed powers M^(2^k) of its transition
+ * matrix, one per set bit of `words`; the Weyl word advances by
+ * words * omega).  The first use of each power builds it on the GPU (2 MiB
+ * each, kept until exit).  Synchronous.  Useful for provably disjoint
+ * substreams: stream i jumped by i * 2^64 would never overlap, here by any
+ * 64-bit distance. */
+xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uint64_t words);
+
 /* ---- serving: continuous batching of requests --------------------------- */
 
 typedef struct {

@@ -70,6 +70,8 @@ SIGNATURES = {
     "xg_transform_normal": [vp, vp, u64, vp],
     "xg_generate_batch": [vp, vp, u32],
     "xg_generate_batch_noalloc": [vp, vp, u32],
+    "xg_set_batch_split": [vp, u64],
+    "xg_jump": [vp, u32, u32, u64],
     "xg_server_start": [vp, vp],
     "xg_server_stop": [vp],
     "xg_submit": [vp, vp, P_u64],
@@ -189,6 +191,14 @@ def xg_generate_batch_noalloc(ctx, items) -> None:
     """items: sequence of (stream, type, count, out_ptr); at most 1024."""
     arr = (XgItem * len(items))(*[XgItem(s, t, c, o) for s, t, c, o in items])
     call("xg_generate_batch_noalloc", ctypes.c_void_p(ctx), arr, len(items))
+
+
+def xg_set_batch_split(ctx, piece_words) -> None:
+    call("xg_set_batch_split", ctypes.c_void_p(ctx), piece_words)
+
+
+def xg_jump(ctx, first, nstreams, words) -> None:
+    call("xg_jump", ctypes.c_void_p(ctx), first, nstreams, words)
 
 
 def xg_server_start(ctx, mem_cap_bytes=0, max_batch=0, lanes=0) -> None:

@@ -132,6 +132,15 @@ class Streams:
         L.xg_generate_batch(self.ctx, [(int(s), TYPES[k] if isinstance(k, str) else int(k), int(c),
                                         0 if o is None else o.data_ptr()) for s, k, c, o in items])
 
+    def set_batch_split(self, piece_words: int):
+        """0: automatic, 1: never cut long calls in batches, else the piece length."""
+        L.xg_set_batch_split(self.ctx, piece_words)
+
+    def jump(self, words: int, first: int = 0, count=None):
+        """Advance streams by `words` positions without generating them."""
+        count = self.n - first if count is None else count
+        L.xg_jump(self.ctx, first, count, words)
+
     def serve(self, mem_cap_bytes: int = 0, max_batch: int = 0, lanes: int = 0) -> "Server":
         return Server(self, mem_cap_bytes, max_batch, lanes)
 

@@ -7,6 +7,7 @@
 #include <numeric>
 #include <unordered_map>
 
+#include "xg_jump.h"
 #include "xg_runtime.h"
 
 namespace xg {
@@ -16,42 +17,82 @@ static uint64_t words_of(uint32_t kind, uint64_t count)
     return kind == kNormal ? count + (count & 1u) : count;
 }
 
-void plan_batch(const HostItem* items, uint32_t n, std::vector<BatchItem>& out,
-                std::vector<uint32_t>& heads, std::vector<uint64_t>& chain_words)
+void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, BatchPlan& plan)
 {
-    out.resize(n);
-    heads.clear();
-    std::unordered_map<uint32_t, uint32_t> last;   // stream -> last item index
-    std::unordered_map<uint32_t, uint32_t> head_of;  // stream -> position in heads
+    plan.units.clear();
+    plan.heads.clear();
+    plan.pieces.clear();
+    plan.piece_stream.clear();
+    plan.piece_skip.clear();
+    plan.piece_index.clear();
+    plan.units_per_item.assign(n, 1u);
+    plan.split_log2 = 0;
+    if (piece_len) {
+        while ((uint64_t(1) << plan.split_log2) < piece_len) ++plan.split_log2;
+        piece_len = uint64_t(1) << plan.split_log2;
+    }
+    // how many items each stream has in this batch
+    std::unordered_map<uint32_t, uint32_t> per_stream;
+    per_stream.reserve(n * 2);
+    for (uint32_t i = 0; i < n; ++i) ++per_stream[items[i].stream];
+    std::unordered_map<uint32_t, uint32_t> last;     // stream -> last unit of its chain
+    std::unordered_map<uint32_t, uint32_t> head_of;  // stream -> its chain's position in heads
     last.reserve(n * 2);
     head_of.reserve(n * 2);
     std::vector<uint64_t> words;
+    auto new_chain = [&](uint32_t unit, uint64_t w) {
+        plan.heads.push_back(unit);
+        words.push_back(w);
+    };
     for (uint32_t i = 0; i < n; ++i) {
         const HostItem& h = items[i];
-        out[i] = BatchItem{h.stream, h.kind, h.count, h.out, h.flag, kNoItem, 0u};
+        const uint64_t w = words_of(h.kind, h.count);
+        if (piece_len && per_stream[h.stream] == 1 && w >= 2 * piece_len) {
+            // cut into pieces; each piece is a one-unit chain of its own
+            const uint64_t npieces = (w + piece_len - 1) / piece_len;
+            plan.units_per_item[i] = (uint32_t)npieces;
+            for (uint64_t m = 0; m < npieces; ++m) {
+                const uint64_t skip = m * piece_len;
+                const uint64_t cnt = std::min<uint64_t>(piece_len, h.count - skip);
+                const uint32_t k = (uint32_t)plan.pieces.size();
+                BatchPiece pc{};
+                pc.item_words = w;
+                pc.last = (m + 1 == npieces) ? 1u : 0u;
+                plan.pieces.push_back(pc);
+                plan.piece_stream.push_back(h.stream);
+                plan.piece_skip.push_back(skip);
+                plan.piece_index.push_back((uint32_t)m);
+                char* out = static_cast<char*>(h.out) + skip * 4;
+                const uint32_t u = (uint32_t)plan.units.size();
+                plan.units.push_back(BatchItem{h.stream, h.kind, cnt, out, h.flag, kNoItem, k + 1});
+                new_chain(u, words_of(h.kind, cnt));
+            }
+            continue;
+        }
+        const uint32_t u = (uint32_t)plan.units.size();
+        plan.units.push_back(BatchItem{h.stream, h.kind, h.count, h.out, h.flag, kNoItem, 0u});
         auto it = last.find(h.stream);
         if (it == last.end()) {
-            head_of[h.stream] = (uint32_t)heads.size();
-            heads.push_back(i);
-            words.push_back(words_of(h.kind, h.count));
-            last[h.stream] = i;
+            head_of[h.stream] = (uint32_t)plan.heads.size();
+            new_chain(u, w);
+            last[h.stream] = u;
         } else {
-            out[it->second].next = i;
-            it->second = i;
-            words[head_of[h.stream]] += words_of(h.kind, h.count);
+            plan.units[it->second].next = u;
+            it->second = u;
+            words[head_of[h.stream]] += w;
         }
     }
-    std::vector<uint32_t> order(heads.size());
+    std::vector<uint32_t> order(plan.heads.size());
     std::iota(order.begin(), order.end(), 0u);
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t a, uint32_t b) { return words[a] > words[b]; });
-    std::vector<uint32_t> sorted(heads.size());
-    chain_words.resize(heads.size());
+    std::vector<uint32_t> sorted(plan.heads.size());
+    plan.chain_words.resize(plan.heads.size());
     for (size_t k = 0; k < order.size(); ++k) {
-        sorted[k] = heads[order[k]];
-        chain_words[k] = words[order[k]];
+        sorted[k] = plan.heads[order[k]];
+        plan.chain_words[k] = words[order[k]];
     }
-    heads.swap(sorted);
+    plan.heads.swap(sorted);
 }
 
 BatchLauncher::~BatchLauncher()
@@ -62,6 +103,8 @@ BatchLauncher::~BatchLauncher()
     if (done_) cudaEventDestroy(done_);
     if (h_staging_) cudaFreeHost(h_staging_);
     if (d_scratch_) cudaFree(d_scratch_);
+    if (h_jstage_) cudaFreeHost(h_jstage_);
+    if (d_jbuf_) cudaFree(d_jbuf_);
 }
 
 bool BatchLauncher::busy() const
@@ -119,22 +162,132 @@ xg_status BatchLauncher::reserve(xg_ctx* c, uint32_t capacity)
     return build_graph(c);
 }
 
-xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s)
+uint64_t BatchLauncher::choose_piece_len(const xg_ctx* c, const HostItem* items, uint32_t n) const
 {
-    if (xg_status st = reserve(c, n)) return st;
+    if (c->split_words == 1) return 0;  // never cut
+    if (c->split_words > 1) return c->split_words;
+    // automatic: aim at units no longer than the batch's words per resident
+    // warp, so that a long call stops being the last warp still running
+    uint64_t total = 0, longest = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint64_t w = words_of(items[i].kind, items[i].count);
+        total += w;
+        longest = std::max(longest, w);
+    }
+    const uint64_t warps = (uint64_t)std::max(1, max_grid_) * 4;
+    uint64_t per_warp = std::max<uint64_t>(1, total / warps);
+    uint64_t len = uint64_t(1) << 16;
+    while (len * 2 <= per_warp && len < (uint64_t(1) << 22)) len *= 2;
+    return longest >= 2 * len ? len : 0;
+}
+
+xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
+{
+    const uint32_t P = (uint32_t)plan_.pieces.size();
+    if (P == 0) return XG_OK;
+    // bit lists: pieces whose index m has bit b set get C_{q+b} applied
+    int top = -1;
+    for (uint32_t m : plan_.piece_index)
+        for (int b = 0; b < 32; ++b)
+            if ((m >> b) & 1u) top = std::max(top, b);
+    std::vector<std::vector<uint32_t>> lists(top + 1);
+    for (uint32_t k = 0; k < P; ++k)
+        for (int b = 0; b <= top; ++b)
+            if ((plan_.piece_index[k] >> b) & 1u) lists[b].push_back(k);
+    size_t nlist = 0, maxlist = 0;
+    for (auto& l : lists) {
+        nlist += l.size();
+        maxlist = std::max(maxlist, l.size());
+    }
+    // device buffer: rings | weyls | streams | skips | lists | tmp
+    const size_t off_rings = 0;
+    const size_t off_weyl = off_rings + (size_t)P * 512;
+    const size_t off_streams = (off_weyl + (size_t)P * 4 + 15) / 16 * 16;
+    const size_t off_skip = (off_streams + (size_t)P * 4 + 15) / 16 * 16;
+    const size_t off_lists = off_skip + (size_t)P * 8;
+    const size_t off_tmp = (off_lists + nlist * 4 + 255) / 256 * 256;
+    const size_t total = off_tmp + std::max<size_t>(maxlist, 1) * 512;
+    if (total > jbytes_) {
+        if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
+        if (h_jstage_) cudaFreeHost(h_jstage_);
+        if (d_jbuf_) cudaFree(d_jbuf_);
+        h_jstage_ = nullptr;
+        d_jbuf_ = nullptr;
+        jbytes_ = 0;
+        const size_t want = total + total / 2;
+        if (cudaHostAlloc(&h_jstage_, want, cudaHostAllocDefault) != cudaSuccess) return XG_ENOMEM;
+        if (cudaMalloc(&d_jbuf_, want) != cudaSuccess) return XG_ENOMEM;
+        jbytes_ = want;
+    }
+    char* hb = static_cast<char*>(h_jstage_);
+    char* db = static_cast<char*>(d_jbuf_);
+    std::memcpy(hb + off_streams, plan_.piece_stream.data(), (size_t)P * 4);
+    std::memcpy(hb + off_skip, plan_.piece_skip.data(), (size_t)P * 8);
+    std::vector<size_t> list_off(lists.size());
+    size_t o = off_lists;
+    for (size_t b = 0; b < lists.size(); ++b) {
+        list_off[b] = o;
+        std::memcpy(hb + o, lists[b].data(), lists[b].size() * 4);
+        o += lists[b].size() * 4;
+    }
+    for (uint32_t k = 0; k < P; ++k) {
+        plan_.pieces[k].ring = reinterpret_cast<const uint32_t*>(db + off_rings + (size_t)k * 512);
+        plan_.pieces[k].weyl0 = reinterpret_cast<const uint32_t*>(db + off_weyl + (size_t)k * 4);
+    }
+    // matrices first (the first use builds them and synchronises)
+    std::vector<const uint64_t*> mats(lists.size(), nullptr);
+    for (size_t b = 0; b < lists.size(); ++b) {
+        if (lists[b].empty()) continue;
+        xg_status st = XG_OK;
+        mats[b] = jump_matrix(c->device, (int)c->param_set, plan_.split_log2 + (int)b, s, &st);
+        if (!mats[b]) return st;
+    }
+    if (cudaMemcpyAsync(db + off_streams, hb + off_streams, off_tmp - off_streams, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return XG_ECUDA;
+    if (launch_gather_rings(c->st, reinterpret_cast<const uint32_t*>(db + off_streams), P,
+                            reinterpret_cast<uint32_t*>(db + off_rings),
+                            reinterpret_cast<const uint64_t*>(db + off_skip),
+                            reinterpret_cast<uint32_t*>(db + off_weyl), 1u, c->weyl_on ? 0x9E3779B9u : 0u,
+                            s) != cudaSuccess)
+        return XG_ECUDA;
+    for (size_t b = 0; b < lists.size(); ++b) {
+        if (lists[b].empty()) continue;
+        if (launch_gf2_apply_listed(mats[b], reinterpret_cast<uint64_t*>(db + off_rings), (uint32_t)lists[b].size(),
+                                    reinterpret_cast<const uint32_t*>(db + list_off[b]),
+                                    reinterpret_cast<uint64_t*>(db + off_tmp), c->sm_count, s) != cudaSuccess)
+            return XG_ECUDA;
+    }
+    return XG_OK;
+}
+
+xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s,
+                                uint32_t* units_per_item)
+{
+    if (!exec_) {
+        if (xg_status st = reserve(c, std::max<uint32_t>(n, 64))) return st;
+    }
     if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
-    std::vector<BatchItem> dev_items;
-    plan_batch(items, n, dev_items, heads_, chain_words_);
+    plan_batch(items, n, choose_piece_len(c, items, n), plan_);
+    const uint32_t nu = (uint32_t)plan_.units.size();
+    if (xg_status st = reserve(c, nu)) return st;
+    if (xg_status st = prologue(c, s)) return st;
+    if (units_per_item) std::memcpy(units_per_item, plan_.units_per_item.data(), (size_t)n * 4);
     char* base = static_cast<char*>(h_staging_);
-    BatchHeader hdr{0u, (uint32_t)heads_.size(), n, capacity_};
+    BatchHeader hdr{0u, (uint32_t)plan_.heads.size(), nu, capacity_};
     std::memcpy(base, &hdr, sizeof hdr);
-    std::memcpy(base + sizeof hdr, heads_.data(), heads_.size() * 4);
-    std::memcpy(base + batch_items_offset(capacity_), dev_items.data(), (size_t)n * sizeof(BatchItem));
-    const size_t used = batch_items_offset(capacity_) + (size_t)n * sizeof(BatchItem);
+    std::memcpy(base + sizeof hdr, plan_.heads.data(), plan_.heads.size() * 4);
+    std::memcpy(base + batch_items_offset(capacity_), plan_.units.data(), (size_t)nu * sizeof(BatchItem));
+    size_t used = batch_items_offset(capacity_) + (size_t)nu * sizeof(BatchItem);
+    if (!plan_.pieces.empty()) {
+        std::memcpy(base + batch_pieces_offset(capacity_), plan_.pieces.data(),
+                    plan_.pieces.size() * sizeof(BatchPiece));
+        used = batch_pieces_offset(capacity_) + plan_.pieces.size() * sizeof(BatchPiece);
+    }
     if (cudaGraphExecMemcpyNodeSetParams1D(exec_, copy_node_, d_scratch_, h_staging_, used,
                                            cudaMemcpyHostToDevice) != cudaSuccess)
         return XG_ECUDA;
-    const unsigned grid = (unsigned)std::min<uint64_t>(max_grid_, (heads_.size() + 3) / 4);
+    const unsigned grid = (unsigned)std::min<uint64_t>(max_grid_, (plan_.heads.size() + 3) / 4);
     args_.st = c->st;
     void* params[] = {&args_};
     cudaKernelNodeParams kp{};
@@ -178,5 +331,15 @@ extern "C" xg_status xg_generate_batch(xg_ctx* ctx, const xg_item* items, uint32
         cudaError_t e = cudaGetLastError();
         return fail(st, "batch launch failed (%s)", cudaGetErrorString(e));
     }
+    return XG_OK;
+}
+
+extern "C" xg_status xg_set_batch_split(xg_ctx* ctx, uint64_t piece_words)
+{
+    using namespace xg;
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if (piece_words > 1 && (piece_words < 64 || (piece_words & (piece_words - 1))))
+        return fail(XG_EINVAL, "piece length must be 0, 1 or a power of two >= 64");
+    ctx->split_words = piece_words;
     return XG_OK;
 }

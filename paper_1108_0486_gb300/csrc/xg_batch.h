@@ -1,7 +1,8 @@
 // Batch launcher: a CUDA graph of two nodes -- copy the batch description
 // from pinned host staging into device scratch, then the persistent batch
 // kernel -- instantiated once per launcher and updated (copy size, grid) per
-// launch.
+// launch.  Long calls alone on their stream are cut into pieces whose start
+// states come from a jump-ahead prologue launched just before the graph.
 #pragma once
 
 #include <cstdint>
@@ -19,25 +20,45 @@ struct HostItem {
     uint32_t kind;
     uint64_t count;
     void* out;
-    uint32_t* flag;  // device pointer of a completion flag, or null
+    uint32_t* flag;  // device pointer of a completion counter, or null
 };
+
+struct BatchPlan {
+    std::vector<BatchItem> units;        // device items (whole calls and pieces)
+    std::vector<uint32_t> heads;         // chain heads, longest chain first
+    std::vector<uint64_t> chain_words;   // words per chain, same order
+    std::vector<BatchPiece> pieces;      // ring/weyl pointers filled at launch
+    std::vector<uint32_t> piece_stream;  // stream of each piece
+    std::vector<uint64_t> piece_skip;    // words of its call before each piece
+    std::vector<uint32_t> piece_index;   // m: the piece starts m * 2^split_log2 words in
+    std::vector<uint32_t> units_per_item;
+    int split_log2 = 0;                  // piece length 2^split_log2 (when pieces exist)
+};
+
+// Plan a batch.  piece_len: 0 = cut nothing, else a power of two; calls alone
+// on their stream with at least 2 * piece_len words are cut into pieces of
+// piece_len words (the last one shorter).
+void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, BatchPlan& plan);
 
 class BatchLauncher {
 public:
     ~BatchLauncher();
-    // Grow to hold `capacity` items (re-creates the graph when it grows).
+    // Grow to hold `capacity` units (re-creates the graph when it grows).
     xg_status reserve(xg_ctx* c, uint32_t capacity);
-    // Build chains (items of one stream, in order), sort chain heads longest
-    // first, stage, and replay the graph on stream s.  Waits first for this
-    // launcher's previous replay to finish reading its staging buffer.
-    xg_status launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s);
-    // Scratch the kernel uses (device), for callers that want its size.
+    // Plan, stage, run the jump prologue if needed, and replay the graph on
+    // stream s.  Waits first for this launcher's previous replay to finish
+    // reading its staging buffers.  units_per_item (optional, n entries)
+    // receives how many completion increments each item will produce.
+    xg_status launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s,
+                     uint32_t* units_per_item = nullptr);
     size_t scratch_bytes() const { return bytes_; }
     cudaEvent_t done_event() const { return done_; }
     bool busy() const;
 
 private:
     xg_status build_graph(xg_ctx* c);
+    xg_status prologue(xg_ctx* c, cudaStream_t s);
+    uint64_t choose_piece_len(const xg_ctx* c, const HostItem* items, uint32_t n) const;
     uint32_t capacity_ = 0;
     size_t bytes_ = 0;
     void* h_staging_ = nullptr;   // pinned
@@ -50,13 +71,11 @@ private:
     bool launched_ = false;
     BatchArgs args_{};
     int max_grid_ = 0;
-    std::vector<uint32_t> heads_;
-    std::vector<uint64_t> chain_words_;
+    BatchPlan plan_;
+    // jump-ahead prologue buffers
+    void* h_jstage_ = nullptr;
+    void* d_jbuf_ = nullptr;
+    size_t jbytes_ = 0;
 };
-
-// Plan a batch on the host: items -> device items with chain links, and the
-// chain heads sorted by total words (longest first).  Exposed for tests.
-void plan_batch(const HostItem* items, uint32_t n, std::vector<BatchItem>& out_items,
-                std::vector<uint32_t>& heads, std::vector<uint64_t>& chain_words);
 
 }  // namespace xg

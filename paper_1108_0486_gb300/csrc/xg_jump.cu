@@ -1,0 +1,299 @@
+// Jump-ahead for xorgens streams.
+//
+// The recurrence of Sec. 2 is linear over GF(2) on the 4096-bit state (the
+// 128-word ring): one step maps a state v to M v.  A stream advanced by J
+// words is M^J v, and with the powers C_k = M^(2^k) at hand, M^J v is the
+// product of the C_k for the set bits of J.  This lets one long stream be cut
+// into pieces that run on different warps (Sec. 2's independent subsequences,
+// here exact consecutive pieces of one sequence) and lets xg_jump skip ahead
+// without generating.  The Weyl word needs no matrix: w + J omega.
+//
+// Matrices are kept in column form: column j of C is the state reached from
+// the unit state e_j (bit j of ring word j/32).  Applying C to v is the XOR of
+// the columns selected by v's bits; squaring is applying C to its own columns.
+// The columns of M itself are one step of the recurrence applied to e_j.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "xg_jump.h"
+#include "xg_kernels.cuh"
+#include "xg_runtime.h"
+
+namespace xg {
+
+constexpr int kBits = 4096;      // state bits
+constexpr int kWords64 = 64;     // uint64 words per state
+constexpr int kApplyVecs = 16;   // states per block in gf2_apply_kernel
+
+// Columns of M for parameter set P: column j = one step from e_j.
+template <class P>
+__global__ void __launch_bounds__(128) step_columns_kernel(uint32_t* __restrict__ cols)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kBits) return;
+    const int wj = j >> 5, bj = j & 31;
+    uint32_t* out = cols + (size_t)j * kR;
+    // the ring shifts by one word: word w of the result is word w+1 of e_j
+    for (int w = 0; w < kR - 1; ++w) out[w] = (w + 1 == wj) ? (1u << bj) : 0u;
+    // the new word: x_{k-r} is ring word 0, x_{k-s} is ring word r - s
+    uint32_t t = (wj == 0) ? (1u << bj) : 0u;
+    uint32_t u = (wj == kR - P::S) ? (1u << bj) : 0u;
+    t ^= t << P::A;
+    t ^= t >> P::B;
+    u ^= u << P::C;
+    u ^= u >> P::D;
+    out[kR - 1] = t ^ u;
+}
+
+// out[i] = C in[i] for the n states listed in idx (or 0..n-1 when idx is
+// null).  64 threads per block, thread t owns uint64 word t of the results;
+// each column of C is loaded once per block and shared by its 16 states.
+// in and out may be the same array: a block reads its states before writing.
+__global__ void __launch_bounds__(64) gf2_apply_kernel(const uint64_t* __restrict__ C, const uint64_t* in,
+                                                       uint64_t* out, uint32_t n, const uint32_t* __restrict__ idx)
+{
+    __shared__ uint64_t vin[kApplyVecs][kWords64];
+    const int t = threadIdx.x;
+    const uint32_t base = blockIdx.x * kApplyVecs;
+    const int nv = (int)umin((uint32_t)kApplyVecs, n - base);
+    for (int v = 0; v < nv; ++v) {
+        const uint32_t i = idx ? idx[base + v] : base + v;
+        vin[v][t] = in[(size_t)i * kWords64 + t];
+    }
+    __syncthreads();
+    uint64_t acc[kApplyVecs];
+#pragma unroll
+    for (int v = 0; v < kApplyVecs; ++v) acc[v] = 0;
+    for (int w = 0; w < kWords64; ++w) {
+        uint64_t bits[kApplyVecs];
+        uint64_t any = 0;
+#pragma unroll
+        for (int v = 0; v < kApplyVecs; ++v) {
+            bits[v] = v < nv ? vin[v][w] : 0ull;
+            any |= bits[v];
+        }
+        while (any) {
+            const int b = __ffsll((long long)any) - 1;
+            any &= any - 1;
+            const uint64_t col = C[(size_t)(w * 64 + b) * kWords64 + t];
+#pragma unroll
+            for (int v = 0; v < kApplyVecs; ++v) acc[v] ^= col & (0ull - ((bits[v] >> b) & 1ull));
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kApplyVecs; ++v) {
+        if (v < nv) {
+            const uint32_t i = idx ? idx[base + v] : base + v;
+            out[(size_t)i * kWords64 + t] = acc[v];
+        }
+    }
+}
+
+// Partial products for few states: block (x, y) handles states
+// [16x, 16x+16) of the list and input words [y*wchunk, (y+1)*wchunk); its
+// XOR goes into tmp[j] (zeroed beforehand) with 64-bit atomic XORs.
+__global__ void __launch_bounds__(64) gf2_apply_partial_kernel(const uint64_t* __restrict__ C,
+                                                               const uint64_t* __restrict__ vecs,
+                                                               const uint32_t* __restrict__ idx, uint32_t n,
+                                                               uint64_t* __restrict__ tmp, int wchunk)
+{
+    __shared__ uint64_t vin[kApplyVecs][kWords64];
+    const int t = threadIdx.x;
+    const uint32_t base = blockIdx.x * kApplyVecs;
+    const int nv = (int)umin((uint32_t)kApplyVecs, n - base);
+    const int w0 = blockIdx.y * wchunk, w1 = min(kWords64, w0 + wchunk);
+    for (int v = 0; v < nv; ++v) vin[v][t] = vecs[(size_t)idx[base + v] * kWords64 + t];
+    __syncthreads();
+    uint64_t acc[kApplyVecs];
+#pragma unroll
+    for (int v = 0; v < kApplyVecs; ++v) acc[v] = 0;
+    for (int w = w0; w < w1; ++w) {
+        uint64_t bits[kApplyVecs];
+        uint64_t any = 0;
+#pragma unroll
+        for (int v = 0; v < kApplyVecs; ++v) {
+            bits[v] = v < nv ? vin[v][w] : 0ull;
+            any |= bits[v];
+        }
+        while (any) {
+            const int b = __ffsll((long long)any) - 1;
+            any &= any - 1;
+            const uint64_t col = C[(size_t)(w * 64 + b) * kWords64 + t];
+#pragma unroll
+            for (int v = 0; v < kApplyVecs; ++v) acc[v] ^= col & (0ull - ((bits[v] >> b) & 1ull));
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kApplyVecs; ++v)
+        if (v < nv && acc[v])
+            atomicXor(reinterpret_cast<unsigned long long*>(&tmp[(size_t)(base + v) * kWords64 + t]),
+                      (unsigned long long)acc[v]);
+}
+
+__global__ void copy_listed_kernel(const uint64_t* __restrict__ tmp, uint64_t* __restrict__ vecs,
+                                   const uint32_t* __restrict__ idx, uint32_t n)
+{
+    const uint32_t j = blockIdx.x;
+    if (j < n) vecs[(size_t)idx[j] * kWords64 + threadIdx.x] = tmp[(size_t)j * kWords64 + threadIdx.x];
+}
+
+// Copy each listed stream's current ring (window at its pend offset) into
+// rings[k]; also rings' Weyl words advanced by skip[k] words.
+__global__ void gather_rings_kernel(State st, const uint32_t* __restrict__ streams, uint32_t n,
+                                    uint32_t* __restrict__ rings, const uint64_t* __restrict__ skip,
+                                    uint32_t* __restrict__ weyl0, uint32_t weyl0_stride, uint32_t omega)
+{
+    const uint32_t k = blockIdx.x;
+    if (k >= n) return;
+    const uint32_t s = streams[k];
+    const uint32_t pend = st.pend[s];
+    const uint32_t* src = st.win + (size_t)s * kWin + (kRingBase - pend);
+    for (int w = threadIdx.x; w < kR; w += blockDim.x) rings[(size_t)k * kR + w] = src[w];
+    if (threadIdx.x == 0 && weyl0)
+        weyl0[(size_t)k * weyl0_stride] = st.weyl[s] + (uint32_t)(skip ? skip[k] : 0) * omega;
+}
+
+// Write jumped rings back as the streams' state (pend = 0; the ring sits at
+// window[kRingBase, kWin)).
+__global__ void scatter_rings_kernel(State st, uint32_t first, uint32_t n, const uint32_t* __restrict__ rings,
+                                     uint64_t jump, uint32_t omega)
+{
+    const uint32_t k = blockIdx.x;
+    if (k >= n) return;
+    const uint32_t s = first + k;
+    uint32_t* dst = st.win + (size_t)s * kWin + kRingBase;
+    for (int w = threadIdx.x; w < kR; w += blockDim.x) dst[w] = rings[(size_t)k * kR + w];
+    if (threadIdx.x == 0) {
+        st.weyl[s] += (uint32_t)jump * omega;
+        st.pend[s] = 0;
+        st.pos[s] += jump;
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+namespace {
+struct Tables {
+    uint64_t* mat[kMaxPow] = {};  // C_k: 4096 columns x 64 uint64 (2 MiB), allocated when built
+    int built = 0;                // C_0 .. C_{built-1} are valid
+};
+std::mutex g_tab_mu;
+Tables g_tabs[64][2];  // per device, per parameter set
+}  // namespace
+
+const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg_status* st)
+{
+    *st = XG_OK;
+    if (device < 0 || device >= 64 || k < 0 || k >= kMaxPow) {
+        *st = fail(XG_EINVAL, "jump power %d out of range", k);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    Tables& T = g_tabs[device][param_set ? 1 : 0];
+    const size_t mat_bytes = (size_t)kBits * kWords64 * 8;
+    bool built_now = false;
+    while (T.built <= k) {
+        const int b = T.built;
+        cudaError_t e = cudaMalloc(&T.mat[b], mat_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            T.mat[b] = nullptr;
+            *st = fail(XG_ENOMEM, "jump tables: cudaMalloc(2 MiB) failed for power %d", b);
+            return nullptr;
+        }
+        if (b == 0) {
+            if (param_set == 1)
+                step_columns_kernel<ParamsPaper><<<kBits / 128, 128, 0, s>>>(reinterpret_cast<uint32_t*>(T.mat[0]));
+            else
+                step_columns_kernel<ParamsDefault><<<kBits / 128, 128, 0, s>>>(reinterpret_cast<uint32_t*>(T.mat[0]));
+        } else {
+            gf2_apply_kernel<<<kBits / kApplyVecs, 64, 0, s>>>(T.mat[b - 1], T.mat[b - 1], T.mat[b], kBits, nullptr);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "jump table build");
+            return nullptr;
+        }
+        T.built = b + 1;
+        built_now = true;
+    }
+    // other CUDA streams may use the tables next: make the build complete
+    if (built_now && cudaStreamSynchronize(s) != cudaSuccess) {
+        *st = cuda_fail(cudaGetLastError(), "jump table build");
+        return nullptr;
+    }
+    return T.mat[k];
+}
+
+cudaError_t launch_gf2_apply(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    gf2_apply_kernel<<<(n + kApplyVecs - 1) / kApplyVecs, 64, 0, s>>>(C, vecs, vecs, n, d_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gf2_apply_listed(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx,
+                                    uint64_t* d_tmp, int sm_count, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint32_t groups = (n + kApplyVecs - 1) / kApplyVecs;
+    int chunks = (int)std::min<uint32_t>(64, std::max<uint32_t>(1, (uint32_t)(4 * sm_count) / groups));
+    while (64 % chunks) --chunks;
+    cudaError_t e = cudaMemsetAsync(d_tmp, 0, (size_t)n * kWords64 * 8, s);
+    if (e != cudaSuccess) return e;
+    gf2_apply_partial_kernel<<<dim3(groups, chunks), 64, 0, s>>>(C, vecs, d_idx, n, d_tmp, 64 / chunks);
+    copy_listed_kernel<<<n, 64, 0, s>>>(d_tmp, vecs, d_idx, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rings(const State& st, const uint32_t* d_streams, uint32_t n, uint32_t* d_rings,
+                                const uint64_t* d_skip, uint32_t* d_weyl0, uint32_t weyl0_stride, uint32_t omega,
+                                cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    gather_rings_kernel<<<n, 128, 0, s>>>(st, d_streams, n, d_rings, d_skip, d_weyl0, weyl0_stride, omega);
+    return cudaGetLastError();
+}
+
+}  // namespace xg
+
+extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uint64_t words)
+{
+    using namespace xg;
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if ((uint64_t)first + nstreams > ctx->n) return fail(XG_EINVAL, "streams out of range");
+    if (ctx->server) return fail(XG_EINVAL, "the request server owns this context; stop it first");
+    if (nstreams == 0 || words == 0) return XG_OK;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t s = ctx->stream;
+    int top = 63;
+    while (!((words >> top) & 1)) --top;
+    xg_status st = XG_OK;
+    for (int k = 0; k <= top; ++k)
+        if (((words >> k) & 1) && !jump_matrix(ctx->device, (int)ctx->param_set, k, s, &st)) return st;
+    uint32_t* rings = nullptr;
+    uint32_t* ids = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)nstreams * kR * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)nstreams * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e, "xg_jump scratch");
+    std::vector<uint32_t> h(nstreams);
+    for (uint32_t i = 0; i < nstreams; ++i) h[i] = first + i;
+    e = cudaMemcpyAsync(ids, h.data(), (size_t)nstreams * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_gather_rings(ctx->st, ids, nstreams, rings, nullptr, nullptr, 0, 0, s);
+    for (int k = 0; k <= top && e == cudaSuccess; ++k) {
+        if (!((words >> k) & 1)) continue;
+        const uint64_t* C = jump_matrix(ctx->device, (int)ctx->param_set, k, s, &st);
+        e = launch_gf2_apply(C, reinterpret_cast<uint64_t*>(rings), nstreams, nullptr, s);
+    }
+    if (e == cudaSuccess) {
+        scatter_rings_kernel<<<nstreams, 128, 0, s>>>(ctx->st, first, nstreams, rings, words,
+                                                      ctx->weyl_on ? 0x9E3779B9u : 0u);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
+    cudaFreeAsync(rings, s);
+    cudaFreeAsync(ids, s);
+    if (e != cudaSuccess) return cuda_fail(e, "xg_jump");
+    return XG_OK;
+}

@@ -1,0 +1,33 @@
+// Jump-ahead: powers of the GF(2) transition matrix and their application.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "xg_launch.h"
+#include "xorgens_gb300.h"
+
+namespace xg {
+
+constexpr int kMaxPow = 64;  // C_k = M^(2^k), k < 64
+
+// C_k for a device and parameter set, built on first use (squarings on
+// stream s; 2 MiB each, kept until the process exits).  Null on failure.
+const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg_status* st);
+
+// vecs[i] = C vecs[i] for the n 512-byte states listed in d_idx (or all).
+cudaError_t launch_gf2_apply(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx,
+                             cudaStream_t s);
+
+// The same for a few listed states at low latency: the columns are split
+// across blocks and combined with atomic XOR into d_tmp (n x 512 bytes).
+cudaError_t launch_gf2_apply_listed(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx,
+                                    uint64_t* d_tmp, int sm_count, cudaStream_t s);
+
+// rings[k] = current ring of stream d_streams[k]; weyl0[k * weyl0_stride] =
+// its Weyl word advanced by d_skip[k] words (weyl0 may be null).
+cudaError_t launch_gather_rings(const State& st, const uint32_t* d_streams, uint32_t n, uint32_t* d_rings,
+                                const uint64_t* d_skip, uint32_t* d_weyl0, uint32_t weyl0_stride, uint32_t omega,
+                                cudaStream_t s);
+
+}  // namespace xg

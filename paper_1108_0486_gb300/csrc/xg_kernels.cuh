@@ -328,6 +328,44 @@ __device__ __forceinline__ float run_stream(const State& st, uint32_t s, uint64_
     return em.acc;
 }
 
+// One piece of a split call (32 lanes, 64-word rounds): the start ring and
+// Weyl word come from the piece table; only the last piece writes the stream
+// state back, as the whole call would have left it.
+template <class P, int OUT, bool VEC>
+__device__ __forceinline__ void run_piece(const State& st, uint32_t s, uint64_t n, uint32_t* row,
+                                          uint32_t omega, int lane, const BatchPiece& pc)
+{
+    using E = Engine<P, 32, 2>;
+    constexpr int RW = E::RW;
+    constexpr bool kNormalOut = (OUT == kNormal);
+    const uint64_t nwords = kNormalOut ? n + (n & 1u) : n;
+    if (nwords == 0) return;
+    Emit<E, OUT, VEC> em;
+    em.acc = 0.0f;
+    E eng;
+    eng.lane = lane;
+    eng.mask = 0xFFFFFFFFu;
+    load_ring(eng, pc.ring - kRingBase, 0u);
+    const uint32_t wp = *pc.weyl0;
+    em.omega = omega;
+    em.limit = n;
+    em.lane_off = (uint64_t)2 * lane;
+    em.wl = wp + (uint32_t)(2 * lane + 1) * omega;
+    em.dst = row + em.lane_off;
+    uint32_t retired[2];
+    const uint64_t nr = (nwords + RW - 1) / RW;
+    const int rot = drive(eng, nr, em, retired);
+    if (pc.last) {
+        __syncwarp();
+        store_window(eng, st.win + (uint64_t)s * kWin, rot, retired);
+        if (lane == 0) {
+            st.weyl[s] = wp + (uint32_t)nwords * omega;
+            st.pend[s] = (uint32_t)(nr * RW - nwords);
+            st.pos[s] += pc.item_words;
+        }
+    }
+}
+
 template <class P, int TPG, int WPL, int OUT, bool VEC>
 __global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
 {
@@ -349,15 +387,35 @@ __global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
 // Persistent batch kernel.  Each warp repeatedly takes the next chain head
 // (atomic counter; heads are sorted longest first by the host), then runs
 // every item of that chain -- the calls on one stream, in order -- with 32
-// lanes per stream and 64-word rounds.  Item types may differ.  When an item
-// has a completion flag, the warp fences its stores system-wide and sets
-// the flag to 1.
+// lanes per stream and 64-word rounds.  Item types may differ.  A long call
+// may arrive cut into pieces (each its own one-item chain) that different
+// warps run at once.  When an item has a completion counter, the warp fences
+// its stores system-wide and adds 1 to it.
 template <class P>
-__device__ __forceinline__ void run_item(const State& st, const BatchItem& it, uint32_t omega, int lane)
+__device__ __forceinline__ void run_item(const State& st, const BatchItem& it, const BatchPiece* pieces,
+                                         uint32_t omega, int lane)
 {
     uint32_t* row = reinterpret_cast<uint32_t*>(it.out);
     const bool vec = (reinterpret_cast<uintptr_t>(row) & 15u) == 0;
     constexpr unsigned kFull = 0xFFFFFFFFu;
+    if (it.piece) {
+        const BatchPiece pc = pieces[it.piece - 1];
+        switch (it.kind) {
+        case kU32:
+            if (vec) run_piece<P, kU32, true>(st, it.stream, it.count, row, omega, lane, pc);
+            else run_piece<P, kU32, false>(st, it.stream, it.count, row, omega, lane, pc);
+            break;
+        case kUniform:
+            if (vec) run_piece<P, kUniform, true>(st, it.stream, it.count, row, omega, lane, pc);
+            else run_piece<P, kUniform, false>(st, it.stream, it.count, row, omega, lane, pc);
+            break;
+        default:
+            if (vec) run_piece<P, kNormal, true>(st, it.stream, it.count, row, omega, lane, pc);
+            else run_piece<P, kNormal, false>(st, it.stream, it.count, row, omega, lane, pc);
+            break;
+        }
+        return;
+    }
     switch (it.kind) {
     case kU32:
         if (vec) run_stream<P, 32, 2, kU32, true>(st, it.stream, it.count, row, omega, lane, kFull);
@@ -384,6 +442,8 @@ __global__ void __launch_bounds__(128) batch_kernel(BatchArgs a)
     const uint32_t* heads = reinterpret_cast<const uint32_t*>(hdr + 1);
     const BatchItem* items = reinterpret_cast<const BatchItem*>(
         reinterpret_cast<const char*>(hdr) + batch_items_offset(hdr->capacity));
+    const BatchPiece* pieces = reinterpret_cast<const BatchPiece*>(
+        reinterpret_cast<const char*>(hdr) + batch_pieces_offset(hdr->capacity));
     for (;;) {
         uint32_t h = 0;
         if (lane == 0) h = atomicAdd(&hdr->counter, 1u);
@@ -392,12 +452,12 @@ __global__ void __launch_bounds__(128) batch_kernel(BatchArgs a)
         uint32_t idx = heads[h];
         while (idx != kNoItem) {
             const BatchItem it = items[idx];
-            run_item<P>(a.st, it, a.omega, lane);
+            run_item<P>(a.st, it, pieces, a.omega, lane);
             __syncwarp(kFull);
             if (it.flag) {
                 __threadfence_system();
                 __syncwarp(kFull);
-                if (lane == 0) *reinterpret_cast<volatile uint32_t*>(it.flag) = 1u;
+                if (lane == 0) atomicAdd_system(it.flag, 1u);
             }
             idx = it.next;
         }

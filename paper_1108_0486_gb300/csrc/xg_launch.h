@@ -51,8 +51,18 @@ struct BatchItem {
     uint32_t kind;     // kU32, kUniform or kNormal
     uint64_t count;    // outputs
     void* out;         // device output (count 4-byte elements)
-    uint32_t* flag;    // device-visible completion flag, or null
+    uint32_t* flag;    // device-visible completion counter (+1 per finished unit), or null
     uint32_t next;     // next item of the same stream (kNoItem: none)
+    uint32_t piece;    // 0: a whole call; k+1: piece k of a split call (BatchPiece k)
+};
+
+// A piece of a long call cut at multiples of a power-of-two length: its start
+// ring and Weyl word come from the jump-ahead prologue, not from the stream.
+struct BatchPiece {
+    const uint32_t* ring;   // 128-word start ring, oldest first
+    const uint32_t* weyl0;  // Weyl word just before the piece's first word
+    uint64_t item_words;    // words of the whole call (the last piece adds them to pos)
+    uint32_t last;          // 1: the call's last piece, which writes the stream state back
     uint32_t pad;
 };
 
@@ -69,9 +79,13 @@ XG_HD inline size_t batch_items_offset(uint32_t capacity)
 {
     return (sizeof(BatchHeader) + (size_t)capacity * 4 + 15) / 16 * 16;
 }
-XG_HD inline size_t batch_scratch_bytes(uint32_t capacity)
+XG_HD inline size_t batch_pieces_offset(uint32_t capacity)
 {
     return batch_items_offset(capacity) + (size_t)capacity * sizeof(BatchItem);
+}
+XG_HD inline size_t batch_scratch_bytes(uint32_t capacity)
+{
+    return batch_pieces_offset(capacity) + (size_t)capacity * sizeof(BatchPiece);
 }
 
 struct BatchArgs {

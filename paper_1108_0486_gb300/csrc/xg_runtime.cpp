@@ -78,12 +78,12 @@ int xg_ctx::pick_block(int kind, int c) const
 xg_status xg_ctx::ensure_staging(size_t bytes)
 {
     if (staging_bytes >= bytes) return XG_OK;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kStage; ++b) {
         if (staging[b]) cudaFree(staging[b]);
         staging[b] = nullptr;
     }
     staging_bytes = 0;
-    for (int b = 0; b < 2; ++b) XG_CUDA(cudaMalloc(&staging[b], bytes), "cudaMalloc(staging)");
+    for (int b = 0; b < kStage; ++b) XG_CUDA(cudaMalloc(&staging[b], bytes), "cudaMalloc(staging)");
     staging_bytes = bytes;
     return XG_OK;
 }
@@ -129,14 +129,15 @@ static bool is_device_pointer(const void* p)
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
-// Host output: generate piece by piece into two device buffers and copy each
-// piece out on a second CUDA stream while the next one is generated.  Pieces
-// split the stream range and, for long requests, each stream's length; the
-// stream positions make consecutive pieces of one stream continue each other.
+// Host output: generate piece by piece into kStage device buffers and copy
+// each piece out on that buffer's own CUDA stream while the next pieces are
+// generated (several copies in flight keep the host link busy).  Pieces split
+// the stream range and, for long requests, each stream's length; the stream
+// positions make consecutive pieces of one stream continue each other.
 static xg_status generate_to_host(Ctx* c, int kind, uint32_t first, uint32_t nstreams, uint64_t n,
                                   void* h_out, uint64_t ld)
 {
-    const size_t kPieceBytes = size_t(256) << 20;
+    const size_t kPieceBytes = size_t(128) << 20;
     xg_status st = c->ensure_staging(kPieceBytes);
     if (st != XG_OK) return st;
     const uint64_t words_per_piece = kPieceBytes / 4;
@@ -155,16 +156,23 @@ static xg_status generate_to_host(Ctx* c, int kind, uint32_t first, uint32_t nst
             st = enqueue_gen(c, kind, first + r0, rows, cols, c->staging[b], ld_stage, nullptr, c->stream);
             if (st != XG_OK) return st;
             XG_CUDA(cudaEventRecord(c->ev_gen[b], c->stream), "cudaEventRecord");
-            XG_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_gen[b], 0), "cudaStreamWaitEvent");
+            XG_CUDA(cudaStreamWaitEvent(c->copy_stream[b], c->ev_gen[b], 0), "cudaStreamWaitEvent");
             char* dst = static_cast<char*>(h_out) + ((uint64_t)r0 * ld + c0) * 4;
-            XG_CUDA(cudaMemcpy2DAsync(dst, ld * 4, c->staging[b], ld_stage * 4, cols * 4, rows,
-                                      cudaMemcpyDeviceToHost, c->copy_stream),
-                    "cudaMemcpy2DAsync(device to host)");
-            XG_CUDA(cudaEventRecord(c->ev_copy[b], c->copy_stream), "cudaEventRecord");
-            b ^= 1;
+            if (ld == ld_stage && cols == ld) {
+                XG_CUDA(cudaMemcpyAsync(dst, c->staging[b], (size_t)rows * cols * 4, cudaMemcpyDeviceToHost,
+                                        c->copy_stream[b]),
+                        "cudaMemcpyAsync(device to host)");
+            } else {
+                XG_CUDA(cudaMemcpy2DAsync(dst, ld * 4, c->staging[b], ld_stage * 4, cols * 4, rows,
+                                          cudaMemcpyDeviceToHost, c->copy_stream[b]),
+                        "cudaMemcpy2DAsync(device to host)");
+            }
+            XG_CUDA(cudaEventRecord(c->ev_copy[b], c->copy_stream[b]), "cudaEventRecord");
+            b = (b + 1) % xg_ctx::kStage;
         }
     }
-    XG_CUDA(cudaStreamSynchronize(c->copy_stream), "cudaStreamSynchronize(copy)");
+    for (int k = 0; k < xg_ctx::kStage; ++k)
+        XG_CUDA(cudaStreamSynchronize(c->copy_stream[k]), "cudaStreamSynchronize(copy)");
     return XG_OK;
 }
 
@@ -230,8 +238,9 @@ xg_status xg_create_streams(xg_ctx** out, uint32_t n_streams, uint32_t param_set
     c->st.pend = reinterpret_cast<uint32_t*>(base + off_pend);
     c->st.pos = reinterpret_cast<uint64_t*>(base + off_pos);
     e = cudaMemsetAsync(c->state_mem, 0, total, c->stream);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    for (int b = 0; b < xg_ctx::kStage && e == cudaSuccess; ++b)
+        e = cudaStreamCreateWithFlags(&c->copy_stream[b], cudaStreamNonBlocking);
+    for (int b = 0; b < xg_ctx::kStage && e == cudaSuccess; ++b) {
         e = cudaEventCreateWithFlags(&c->ev_gen[b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_copy[b], cudaEventDisableTiming);
     }
@@ -255,11 +264,13 @@ xg_status xg_destroy(xg_ctx* ctx)
         c->batch[b] = nullptr;
     }
     if (c->stream || c->state_mem) cudaStreamSynchronize(c->stream);
-    if (c->copy_stream) {
-        cudaStreamSynchronize(c->copy_stream);
-        cudaStreamDestroy(c->copy_stream);
+    for (int b = 0; b < xg_ctx::kStage; ++b) {
+        if (c->copy_stream[b]) {
+            cudaStreamSynchronize(c->copy_stream[b]);
+            cudaStreamDestroy(c->copy_stream[b]);
+        }
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < xg_ctx::kStage; ++b) {
         if (c->ev_gen[b]) cudaEventDestroy(c->ev_gen[b]);
         if (c->ev_copy[b]) cudaEventDestroy(c->ev_copy[b]);
         if (c->staging[b]) cudaFree(c->staging[b]);

@@ -29,16 +29,18 @@ struct xg_ctx {
     int cfg[3] = {-1, -1, -1};      // per output type; -1 = automatic
     int blk[3] = {0, 0, 0};         // tuned threads per block per output type; 0 = the cfg's default
     int block[xg::kNumCfgs] = {};   // threads per block per configuration
-    // host-output staging
-    void* staging[2] = {nullptr, nullptr};
+    // host-output staging: kStage device buffers, each with its own copy stream
+    static constexpr int kStage = 4;
+    void* staging[kStage] = {};
     size_t staging_bytes = 0;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_gen[2] = {nullptr, nullptr};
-    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream[kStage] = {};
+    cudaEvent_t ev_gen[kStage] = {};
+    cudaEvent_t ev_copy[kStage] = {};
     std::mutex mu;
     xg::Server* server = nullptr;
     xg::BatchLauncher* batch[2] = {nullptr, nullptr};
     int batch_next = 0;
+    uint64_t split_words = 0;  // batch piece length: 0 automatic, 1 never, else forced
 
     int pick_cfg(int kind, uint32_t nstreams) const;
     int pick_block(int kind, int cfg) const;

@@ -111,6 +111,7 @@ struct Ticket {
     bool pooled = false;
     size_t bytes = 0;
     uint32_t slot = 0;
+    uint32_t expected = 1;      // completion increments: 1, or the pieces it was cut into
     std::atomic<int> state{0};  // kQueued, kRunning, kDone, kFailed
     uint64_t t_submit = 0, t_launch = 0;
     std::atomic<uint64_t> t_done{0};
@@ -219,7 +220,7 @@ public:
         if (st == kDone || st == kFailed) return true;
         if (t.state.load(std::memory_order_acquire) != kRunning) return false;
         volatile uint32_t* f = h_flags_ + t.slot;
-        if (*f == 0) return false;
+        if (*f < t.expected) return false;
         int expect = kRunning;
         if (t.state.compare_exchange_strong(expect, kDone)) t.t_done.store(now_ns());
         return true;
@@ -262,8 +263,8 @@ public:
         if (t.state.load() != kDone && t.state.load() != kFailed) {
             // the scheduler may not have seen the flag yet
             volatile uint32_t* f = h_flags_ + t.slot;
-            if (!(t.state.load() == kRunning && *f)) return fail(XG_EINVAL, "ticket %llu still in flight",
-                                                                 (unsigned long long)id);
+            if (!(t.state.load() == kRunning && *f >= t.expected))
+                return fail(XG_EINVAL, "ticket %llu still in flight", (unsigned long long)id);
         }
         if (t.pooled) pool_.release(t.out);
         outstanding_ -= t.bytes;
@@ -308,6 +309,7 @@ private:
     {
         std::vector<std::shared_ptr<Ticket>> fresh;
         std::vector<HostItem> items;
+        std::vector<uint32_t> units;
         while (run_.load()) {
             bool progress = false;
             {
@@ -376,14 +378,20 @@ private:
                     busy_streams_.insert(s);
                     t->slot = (uint32_t)(li * cfg_.max_batch + items.size());
                     t->t_launch = t_launch;
-                    t->state.store(kRunning, std::memory_order_release);
                     items.push_back(HostItem{s, t->req.type, t->req.count, t->out, d_flags_ + t->slot});
                     l.inflight.push_back(t);
                     --queued_;
                 }
                 if (items.empty()) continue;
                 in_flight_ += items.size();
-                if (l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream) != XG_OK) {
+                units.resize(items.size());
+                const xg_status lst = l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream,
+                                                         units.data());
+                for (size_t j = 0; j < l.inflight.size(); ++j) {
+                    l.inflight[j]->expected = lst == XG_OK ? units[j] : 1u;
+                    l.inflight[j]->state.store(kRunning, std::memory_order_release);
+                }
+                if (lst != XG_OK) {
                     cudaGetLastError();
                     launch_error_ = true;
                     for (auto& t : l.inflight) fail_ticket(t);

@@ -252,3 +252,74 @@ def test_autotune_picks_a_supported_launch_and_leaves_streams_in_place(kind):
     ref = O.streams(seeds, 77 + nwords(kind, 3001))[:, 77:]
     for i in (0, 999, 1999):
         check(kind, got[i, :3001], oracle_call(ref[i], kind, 3001))
+
+
+# ------------------------------------------------------------ jump-ahead
+
+@pytest.mark.parametrize("ps", [0, 1])
+def test_jump_matches_stepping(ps):
+    seeds = W.seeds(6, start=40)
+    for J in (1, 63, 64, 4095, 4096, 65537, 1_000_003):
+        with Streams(6, param_set=ps, seeds=seeds) as st:
+            st.u32(7)          # not at a round boundary
+            st.jump(J)
+            got = st.u32(500).cpu().numpy().view(np.uint32)
+        for i in (0, 5):
+            ref = O.Xorgens.param_set(ps).seed(int(seeds[i])).u32(7 + J + 500)[7 + J:]
+            assert np.array_equal(got[i], ref), (ps, J, i)
+
+
+def test_jump_composes_for_large_distances():
+    seeds = W.seeds(4)
+    a, b = (1 << 40) + 12345, (1 << 37) + 999
+    with Streams(4, seeds=seeds) as x, Streams(4, seeds=seeds) as y:
+        x.jump(a)
+        x.jump(b)
+        y.jump(a + b)
+        assert torch.equal(x.u32(300), y.u32(300))
+        x.jump(1 << 63)
+        y.jump(1 << 62)
+        y.jump(1 << 62)
+        assert torch.equal(x.normal(301), y.normal(301))
+
+
+@pytest.mark.parametrize("piece", [64, 1024])
+def test_batch_cut_into_pieces_equals_uncut(piece):
+    rng = np.random.default_rng(31)
+    seeds = W.seeds(90)
+    items = [(i, KINDS[i % 3], int(rng.integers(1, 60000))) for i in range(90)]
+    items += [(90 // 2, "u32", 5000), (3, "normal", 777)]  # streams with two items stay whole
+    with Streams(90, seeds=seeds) as a, Streams(90, seeds=seeds) as b:
+        a.set_batch_split(piece)
+        b.set_batch_split(1)
+        oa = [alloc(k, n) for _, k, n in items]
+        ob = [alloc(k, n) for _, k, n in items]
+        a.batch([(s, k, n, o) for (s, k, n), o in zip(items, oa)])
+        b.batch([(s, k, n, o) for (s, k, n), o in zip(items, ob)])
+        for (s, k, n), x, y in zip(items, oa, ob):
+            assert torch.equal(x[:n], y[:n]), (s, k, n)
+        assert torch.equal(a.u32(129), b.u32(129))  # same state afterwards
+    refs = oracle_per_item(seeds, items)
+    for j in (0, 1, 2, 50, 89, 90, 91):
+        s, k, n = items[j]
+        check(k, oa[j][:n], refs[j])
+
+
+def test_server_with_cut_requests():
+    rng = np.random.default_rng(13)
+    S = 64
+    seeds = W.seeds(S, start=200)
+    reqs = random_items(rng, S, 150, max_len=300000)
+    outs = [alloc(k, n) for _, k, n in reqs]
+    with Streams(S, seeds=seeds) as st:
+        st.set_batch_split(4096)
+        srv = st.serve(lanes=4, max_batch=32)
+        tickets = [srv.submit(s, k, n, out=o) for (s, k, n), o in zip(reqs, outs)]
+        for t in tickets:
+            srv.wait(t, 60000)
+        for t in tickets:
+            srv.release(t)
+        srv.stop()
+    refs = oracle_per_item(seeds, reqs)
+    for (s, k, n), o, ref in zip(reqs, outs, refs):
+        check(k, o[:n], ref)
