@@ -77,6 +77,23 @@ def _dist():
     return ws, rank, local
 
 
+def rank_seeds(rank: int):
+    """Weak scaling: every rank owns its own 16384 streams, seeded with
+    consecutive integers that no other rank uses."""
+    return W.seeds(STREAMS, start=1 + rank * STREAMS)
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The job's time is the slowest rank's (no data-path collective: the
+    streams are independent; only the timing is reduced)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -229,7 +246,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     # weak scaling: every rank owns its own 16384 streams (seeds offset by rank)
-    seeds = W.seeds(STREAMS, start=1 + rank * STREAMS)
+    seeds = rank_seeds(rank)
     st = Streams(STREAMS, seeds=seeds, stream=stream)
     buf_u = torch.empty((STREAMS, N_PER), dtype=torch.int32, device="cuda")
     buf_f = torch.empty((STREAMS, N_PER), dtype=torch.float32, device="cuda")
@@ -272,10 +289,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms = t_start.elapsed_time(t_end)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_u = [a.elapsed_time(b) for a, b, _ in ev]
     ms_f = [b.elapsed_time(c) for _, b, c in ev]
     rns_per_step = STREAMS * N_PER * 2
@@ -297,6 +311,10 @@ def run_ours(args):
         rows = extra_rows(st, stream, torch, peak)
         rows["batched"] = batched_row(torch, L, stream, peak)
         rows["serving"] = serving_row(torch, L, stream, seconds=args.serve_seconds)
+        try:
+            rows["curand_xorwow_context"] = curand_row(torch, stream)
+        except Exception as e:  # context only: never fail the bench on it
+            rows["curand_xorwow_context"] = {"unavailable": str(e)[:200]}
     e2e = None
     if not args.no_e2e:
         e2e = end_to_end(st, stream, torch, L, args)
@@ -365,9 +383,10 @@ def batched_row(torch, L, stream, peak, reps=3):
             for it in items]
     st = Streams(len(items), seeds=seeds, stream=stream)
     spec = [(it.stream, it.kind, it.count, o.data_ptr()) for it, o in zip(items, outs)]
-    ms = _time(lambda: L.xg_generate_batch(st.ctx, spec), stream, torch, reps=reps, warm=1)
+    arr = L.make_items(spec)  # built once, outside the timed region
+    ms = _time(lambda: L.xg_generate_batch(st.ctx, arr), stream, torch, reps=reps, warm=1)
     longest = max(range(len(items)), key=lambda i: items[i].count)
-    one = [spec[longest]]
+    one = L.make_items([spec[longest]])
     ms_long = _time(lambda: L.xg_generate_batch(st.ctx, one), stream, torch, reps=reps, warm=1)
     st.close()
     del outs
@@ -393,32 +412,19 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0)
     st = Streams(S, seeds=W.seeds(S), stream=stream)
     torch.cuda.synchronize()
     L.xg_server_start(st.ctx, 16 << 30, 1024, 16)
-    tickets = []
-    lock = th.Lock()
     done_times = []
     refused = [0]
-    stop = [False]
+    n_total = len(reqs)
+    cbuf = (L.XgCompletion * 4096)()
 
     def reaper():
-        pending = []
-        while True:
-            with lock:
-                pending.extend(tickets)
-                tickets.clear()
-            still = []
-            for t in pending:
-                done, _ = L.xg_poll(st.ctx, t)
-                if done:
-                    done_times.append(L.xg_ticket_times(st.ctx, t))
-                    L.xg_release(st.ctx, t)
-                else:
-                    still.append(t)
-            pending = still
-            if stop[0] and not pending:
-                with lock:
-                    if not tickets:
-                        return
-            time.sleep(0.0002)
+        # bulk drain: one call returns (and releases) every finished request
+        while len(done_times) < n_total:
+            got = L.xg_collect(st.ctx, release=True, buf=cbuf)
+            for _, ts, tl, td, status, _ in got:
+                done_times.append((ts, tl, td))
+            if not got:
+                time.sleep(0.0002)
 
     old_switch = sys.getswitchinterval()
     sys.setswitchinterval(1e-4)
@@ -433,16 +439,13 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0)
             pass
         while True:
             try:
-                t = L.xg_submit(st.ctx, r.stream, r.kind, r.count, 0)
+                L.xg_submit(st.ctx, r.stream, r.kind, r.count, 0)
                 break
             except L.XGError as e:
                 if e.status != L.XG_EAGAIN:
                     raise
                 refused[0] += 1
                 time.sleep(0.0001)
-        with lock:
-            tickets.append(t)
-    stop[0] = True
     rt.join()
     sys.setswitchinterval(old_switch)
     wall = time.perf_counter() - t0
@@ -487,6 +490,33 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0)
         "note": "same arrivals; a single CUDA stream serialises the launches, so the queue grows"}
     st.close()
     return row
+
+
+def curand_row(torch, stream, n=1 << 30):
+    """Context only: NVIDIA's XORWOW generator (the CURAND row of the paper's
+    Table 1) timed through the cuRAND host API on the same GPU, 2^30 u32 and
+    2^30 FP32 normals.  A library call with no parity claim."""
+    import ctypes
+    import glob
+    paths = sorted(glob.glob("/usr/local/cuda/lib64/libcurand.so*") +
+                   glob.glob("/usr/local/cuda/targets/*/lib/libcurand.so*"))
+    if not paths:
+        return {"unavailable": "libcurand not found"}
+    lib = ctypes.CDLL(paths[0])
+    gen = ctypes.c_void_p()
+    if lib.curandCreateGenerator(ctypes.byref(gen), 101):  # CURAND_RNG_PSEUDO_XORWOW
+        return {"unavailable": "curandCreateGenerator failed"}
+    lib.curandSetStream(gen, ctypes.c_void_p(stream.cuda_stream))
+    lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(1108))
+    buf = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = ctypes.c_void_p(buf.data_ptr())
+    ms_u = _time(lambda: lib.curandGenerate(gen, p, ctypes.c_size_t(n)), stream, torch)
+    ms_n = _time(lambda: lib.curandGenerateNormal(gen, p, ctypes.c_size_t(n), ctypes.c_float(0.0),
+                                                  ctypes.c_float(1.0)), stream, torch)
+    lib.curandDestroyGenerator(gen)
+    del buf
+    return {"generator": "cuRAND XORWOW (library, context only)", "u32_rn_s": n / (ms_u / 1e3),
+            "normal_rn_s": n / (ms_n / 1e3), "u32_ms": ms_u, "normal_ms": ms_n}
 
 
 def end_to_end(st, stream, torch, L, args):

@@ -233,7 +233,11 @@ typedef struct {
  * (one replay of the persistent batch kernel's graph).  Batches on different
  * lanes run concurrently, so requests that arrive while others are on the
  * GPU start as soon as a lane and memory free up.  Each result is identical
- * to the same request run alone. */
+ * to the same request run alone.  A request whose batch fails to launch is
+ * reported as XG_EDEVICE by xg_poll / xg_wait and leaves its stream where it
+ * was; the server keeps serving.  (For testing that path without a GPU
+ * fault, the environment variable XG_INJECT_LAUNCH_FAILURES=N, read at
+ * start, makes the first N batch launches fail on the host.) */
 xg_status xg_server_start(xg_ctx* ctx, const xg_server_config* cfg);
 
 /* Stop the server thread after the batches in flight finish; frees the pool
@@ -261,6 +265,22 @@ xg_status xg_ticket_times(xg_ctx* ctx, uint64_t ticket, uint64_t* t_submit_ns,
                           uint64_t* t_launch_ns, uint64_t* t_done_ns);
 
 xg_status xg_server_stats_get(xg_ctx* ctx, xg_server_stats* out);
+
+typedef struct {
+    uint64_t ticket;
+    uint64_t t_submit_ns, t_launch_ns, t_done_ns; /* server clock */
+    int32_t status;                               /* XG_OK, or XG_EDEVICE if its batch failed */
+    uint32_t pad;
+    void* d_result;                               /* output pointer (NULL once released) */
+} xg_completion;
+
+/* Drain finished requests in bulk: up to max of them, oldest completion
+ * first, into out[0 .. *n_out).  With release != 0 each is also released as
+ * by xg_release (a pool buffer is then gone: use it only for requests whose
+ * output went to caller memory, or whose data is no longer needed).  Each
+ * finished ticket is reported once; tickets released by their owner before
+ * they are collected are skipped. */
+xg_status xg_collect(xg_ctx* ctx, xg_completion* out, uint32_t max, uint32_t* n_out, int release);
 
 /* ---- launch configuration --------------------------------------------- */
 

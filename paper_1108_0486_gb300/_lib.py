@@ -47,6 +47,12 @@ class XgServerConfig(ctypes.Structure):
                 ("lanes", ctypes.c_uint32)]
 
 
+class XgCompletion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64),
+                ("t_launch_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_uint32), ("d_result", ctypes.c_void_p)]
+
+
 class XgServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "submitted", "completed", "refused", "queued", "in_flight", "batches", "items_launched",
@@ -80,6 +86,7 @@ SIGNATURES = {
     "xg_release": [vp, u64],
     "xg_ticket_times": [vp, u64, P_u64, P_u64, P_u64],
     "xg_server_stats_get": [vp, vp],
+    "xg_collect": [vp, vp, u32, P_u32, i32],
     "xg_set_launch": [vp, i32, u32, u32],
     "xg_get_launch": [vp, i32, P_u32, P_u32],
     "xg_autotune": [vp, i32, u32, u64, P_u32, P_u32, P_u32, ctypes.POINTER(ctypes.c_float)],
@@ -181,16 +188,32 @@ def xg_transform_normal(ctx, words_ptr, n, out_ptr) -> None:
     call("xg_transform_normal", ctypes.c_void_p(ctx), ctypes.c_void_p(words_ptr), n, ctypes.c_void_p(out_ptr))
 
 
+def make_items(items):
+    """A ctypes xg_item array from (stream, type, count, out_ptr) tuples (build
+    it once to reuse it across calls)."""
+    if isinstance(items, ctypes.Array):
+        return items
+    import numpy as np
+    a = np.asarray(items, dtype=np.uint64).reshape(-1, 4)
+    rec = np.zeros(a.shape[0], dtype=[("stream", "<u4"), ("type", "<u4"), ("count", "<u8"),
+                                     ("out", "<u8")])
+    rec["stream"], rec["type"], rec["count"], rec["out"] = a[:, 0], a[:, 1], a[:, 2], a[:, 3]
+    arr = (XgItem * a.shape[0])()
+    ctypes.memmove(arr, rec.ctypes.data, rec.nbytes)
+    return arr
+
+
 def xg_generate_batch(ctx, items) -> None:
-    """items: sequence of (stream, type, count, out_ptr)."""
-    arr = (XgItem * len(items))(*[XgItem(s, t, c, o) for s, t, c, o in items])
-    call("xg_generate_batch", ctypes.c_void_p(ctx), arr, len(items))
+    """items: sequence of (stream, type, count, out_ptr), or a make_items() array."""
+    arr = make_items(items)
+    call("xg_generate_batch", ctypes.c_void_p(ctx), arr, len(arr))
 
 
 def xg_generate_batch_noalloc(ctx, items) -> None:
-    """items: sequence of (stream, type, count, out_ptr); at most 1024."""
-    arr = (XgItem * len(items))(*[XgItem(s, t, c, o) for s, t, c, o in items])
-    call("xg_generate_batch_noalloc", ctypes.c_void_p(ctx), arr, len(items))
+    """items: sequence of (stream, type, count, out_ptr), or a make_items()
+    array; at most 1024."""
+    arr = make_items(items)
+    call("xg_generate_batch_noalloc", ctypes.c_void_p(ctx), arr, len(arr))
 
 
 def xg_set_batch_split(ctx, piece_words) -> None:
@@ -237,6 +260,15 @@ def xg_ticket_times(ctx, ticket):
     a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     call("xg_ticket_times", ctypes.c_void_p(ctx), ticket, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
     return a.value, b.value, c.value
+
+
+def xg_collect(ctx, max_n=4096, release=False, buf=None):
+    """Finished tickets as a list of (ticket, t_submit, t_launch, t_done, status, d_result)."""
+    arr = buf if buf is not None else (XgCompletion * max_n)()
+    n = ctypes.c_uint32()
+    call("xg_collect", ctypes.c_void_p(ctx), arr, len(arr), ctypes.byref(n), int(bool(release)))
+    return [(c.ticket, c.t_submit_ns, c.t_launch_ns, c.t_done_ns, c.status, c.d_result)
+            for c in arr[: n.value]]
 
 
 def xg_server_stats_get(ctx) -> dict:

@@ -173,6 +173,10 @@ class Server:
     def stats(self) -> dict:
         return L.xg_server_stats_get(self.ctx)
 
+    def collect(self, max_n: int = 4096, release: bool = False):
+        """Finished tickets: (ticket, t_submit, t_launch, t_done, status, d_result)."""
+        return L.xg_collect(self.ctx, max_n, release)
+
     def result(self, ticket: int, kind, count: int, timeout_ms: int = 10000) -> torch.Tensor:
         """Wait for a ticket and view its output as a tensor (no copy)."""
         ptr = self.wait(ticket, timeout_ms)

@@ -5,7 +5,6 @@
 #include <cstring>
 #include <new>
 #include <numeric>
-#include <unordered_map>
 
 #include "xg_jump.h"
 #include "xg_runtime.h"
@@ -17,7 +16,7 @@ static uint64_t words_of(uint32_t kind, uint64_t count)
     return kind == kNormal ? count + (count & 1u) : count;
 }
 
-void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, BatchPlan& plan)
+void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan)
 {
     plan.units.clear();
     plan.heads.clear();
@@ -31,23 +30,24 @@ void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, BatchPlan
         while ((uint64_t(1) << plan.split_log2) < piece_len) ++plan.split_log2;
         piece_len = uint64_t(1) << plan.split_log2;
     }
-    // how many items each stream has in this batch
-    std::unordered_map<uint32_t, uint32_t> per_stream;
-    per_stream.reserve(n * 2);
-    for (uint32_t i = 0; i < n; ++i) ++per_stream[items[i].stream];
-    std::unordered_map<uint32_t, uint32_t> last;     // stream -> last unit of its chain
-    std::unordered_map<uint32_t, uint32_t> head_of;  // stream -> its chain's position in heads
-    last.reserve(n * 2);
-    head_of.reserve(n * 2);
+    if (plan.items_of_stream.size() < n_streams) {
+        plan.items_of_stream.assign(n_streams, 0u);
+        plan.last_unit.assign(n_streams, 0u);
+        plan.chain_of.assign(n_streams, 0u);
+    }
+    // stream -> items in this batch; last unit of its chain + 1; its chain + 1
+    auto& count = plan.items_of_stream;
+    auto& last = plan.last_unit;
+    auto& chain = plan.chain_of;
+    for (uint32_t i = 0; i < n; ++i) ++count[items[i].stream];
+    plan.units.reserve(n);
+    plan.heads.reserve(n);
     std::vector<uint64_t> words;
-    auto new_chain = [&](uint32_t unit, uint64_t w) {
-        plan.heads.push_back(unit);
-        words.push_back(w);
-    };
+    words.reserve(n);
     for (uint32_t i = 0; i < n; ++i) {
         const HostItem& h = items[i];
         const uint64_t w = words_of(h.kind, h.count);
-        if (piece_len && per_stream[h.stream] == 1 && w >= 2 * piece_len) {
+        if (piece_len && count[h.stream] == 1 && w >= 2 * piece_len) {
             // cut into pieces; each piece is a one-unit chain of its own
             const uint64_t npieces = (w + piece_len - 1) / piece_len;
             plan.units_per_item[i] = (uint32_t)npieces;
@@ -63,24 +63,28 @@ void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, BatchPlan
                 plan.piece_skip.push_back(skip);
                 plan.piece_index.push_back((uint32_t)m);
                 char* out = static_cast<char*>(h.out) + skip * 4;
-                const uint32_t u = (uint32_t)plan.units.size();
+                plan.heads.push_back((uint32_t)plan.units.size());
+                words.push_back(words_of(h.kind, cnt));
                 plan.units.push_back(BatchItem{h.stream, h.kind, cnt, out, h.flag, kNoItem, k + 1});
-                new_chain(u, words_of(h.kind, cnt));
             }
             continue;
         }
         const uint32_t u = (uint32_t)plan.units.size();
         plan.units.push_back(BatchItem{h.stream, h.kind, h.count, h.out, h.flag, kNoItem, 0u});
-        auto it = last.find(h.stream);
-        if (it == last.end()) {
-            head_of[h.stream] = (uint32_t)plan.heads.size();
-            new_chain(u, w);
-            last[h.stream] = u;
+        if (last[h.stream] == 0) {
+            chain[h.stream] = (uint32_t)plan.heads.size() + 1;
+            plan.heads.push_back(u);
+            words.push_back(w);
         } else {
-            plan.units[it->second].next = u;
-            it->second = u;
-            words[head_of[h.stream]] += w;
+            plan.units[last[h.stream] - 1].next = u;
+            words[chain[h.stream] - 1] += w;
         }
+        last[h.stream] = u + 1;
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        count[items[i].stream] = 0;
+        last[items[i].stream] = 0;
+        chain[items[i].stream] = 0;
     }
     std::vector<uint32_t> order(plan.heads.size());
     std::iota(order.begin(), order.end(), 0u);
@@ -181,32 +185,38 @@ uint64_t BatchLauncher::choose_piece_len(const xg_ctx* c, const HostItem* items,
     return longest >= 2 * len ? len : 0;
 }
 
+// Start rings of the pieces.  Piece 0 of a call gets the stream's ring
+// (gather).  Then, doubling: step b gives every piece m in [2^b, 2^(b+1)) the
+// ring of piece m - 2^b advanced by 2^b pieces, i.e. C_{q+b} applied to it
+// (q = log2 of the piece length).  Each piece costs one application and a
+// call cut into K pieces needs ceil(log2 K) steps.
 xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
 {
     const uint32_t P = (uint32_t)plan_.pieces.size();
     if (P == 0) return XG_OK;
-    // bit lists: pieces whose index m has bit b set get C_{q+b} applied
-    int top = -1;
-    for (uint32_t m : plan_.piece_index)
-        for (int b = 0; b < 32; ++b)
-            if ((m >> b) & 1u) top = std::max(top, b);
-    std::vector<std::vector<uint32_t>> lists(top + 1);
-    for (uint32_t k = 0; k < P; ++k)
-        for (int b = 0; b <= top; ++b)
-            if ((plan_.piece_index[k] >> b) & 1u) lists[b].push_back(k);
-    size_t nlist = 0, maxlist = 0;
-    for (auto& l : lists) {
-        nlist += l.size();
-        maxlist = std::max(maxlist, l.size());
+    // per step b: (src, dst) piece pairs; pieces of one call are consecutive
+    std::vector<std::vector<uint32_t>> src, dst;
+    for (uint32_t k = 0; k < P; ++k) {
+        const uint32_t m = plan_.piece_index[k];
+        if (m == 0) continue;
+        int b = 31;
+        while (!((m >> b) & 1u)) --b;
+        if ((int)src.size() <= b) {
+            src.resize(b + 1);
+            dst.resize(b + 1);
+        }
+        src[b].push_back(k - (1u << b));
+        dst[b].push_back(k);
     }
-    // device buffer: rings | weyls | streams | skips | lists | tmp
+    size_t npairs = 0;
+    for (auto& l : src) npairs += l.size();
+    // device buffer: rings | weyls | gather streams | gather skips (zeros) | gather ids | pair lists
     const size_t off_rings = 0;
     const size_t off_weyl = off_rings + (size_t)P * 512;
     const size_t off_streams = (off_weyl + (size_t)P * 4 + 15) / 16 * 16;
     const size_t off_skip = (off_streams + (size_t)P * 4 + 15) / 16 * 16;
     const size_t off_lists = off_skip + (size_t)P * 8;
-    const size_t off_tmp = (off_lists + nlist * 4 + 255) / 256 * 256;
-    const size_t total = off_tmp + std::max<size_t>(maxlist, 1) * 512;
+    const size_t total = off_lists + 2 * npairs * 4 + 16;
     if (total > jbytes_) {
         if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
         if (h_jstage_) cudaFreeHost(h_jstage_);
@@ -221,41 +231,52 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
     }
     char* hb = static_cast<char*>(h_jstage_);
     char* db = static_cast<char*>(d_jbuf_);
-    std::memcpy(hb + off_streams, plan_.piece_stream.data(), (size_t)P * 4);
-    std::memcpy(hb + off_skip, plan_.piece_skip.data(), (size_t)P * 8);
-    std::vector<size_t> list_off(lists.size());
+    // every piece's Weyl word comes from the gather (its own skip); its ring
+    // from the gather (m = 0) or a doubling step
+    for (uint32_t k = 0; k < P; ++k) {
+        reinterpret_cast<uint32_t*>(hb + off_streams)[k] = plan_.piece_stream[k];
+        reinterpret_cast<uint64_t*>(hb + off_skip)[k] = plan_.piece_skip[k];
+    }
+    std::vector<size_t> src_off(src.size()), dst_off(src.size());
     size_t o = off_lists;
-    for (size_t b = 0; b < lists.size(); ++b) {
-        list_off[b] = o;
-        std::memcpy(hb + o, lists[b].data(), lists[b].size() * 4);
-        o += lists[b].size() * 4;
+    for (size_t b = 0; b < src.size(); ++b) {
+        src_off[b] = o;
+        std::memcpy(hb + o, src[b].data(), src[b].size() * 4);
+        o += src[b].size() * 4;
+        dst_off[b] = o;
+        std::memcpy(hb + o, dst[b].data(), dst[b].size() * 4);
+        o += dst[b].size() * 4;
     }
     for (uint32_t k = 0; k < P; ++k) {
         plan_.pieces[k].ring = reinterpret_cast<const uint32_t*>(db + off_rings + (size_t)k * 512);
         plan_.pieces[k].weyl0 = reinterpret_cast<const uint32_t*>(db + off_weyl + (size_t)k * 4);
     }
     // matrices first (the first use builds them and synchronises)
-    std::vector<const uint64_t*> mats(lists.size(), nullptr);
-    for (size_t b = 0; b < lists.size(); ++b) {
-        if (lists[b].empty()) continue;
+    std::vector<const uint64_t*> mats(src.size(), nullptr);
+    for (size_t b = 0; b < src.size(); ++b) {
+        if (src[b].empty()) continue;
         xg_status st = XG_OK;
         mats[b] = jump_matrix(c->device, (int)c->param_set, plan_.split_log2 + (int)b, s, &st);
         if (!mats[b]) return st;
     }
-    if (cudaMemcpyAsync(db + off_streams, hb + off_streams, off_tmp - off_streams, cudaMemcpyHostToDevice, s) !=
+    if (cudaMemcpyAsync(db + off_streams, hb + off_streams, o - off_streams, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return XG_ECUDA;
+    // all rings gathered (the doubling steps overwrite the m > 0 ones: zero them first)
     if (launch_gather_rings(c->st, reinterpret_cast<const uint32_t*>(db + off_streams), P,
                             reinterpret_cast<uint32_t*>(db + off_rings),
                             reinterpret_cast<const uint64_t*>(db + off_skip),
                             reinterpret_cast<uint32_t*>(db + off_weyl), 1u, c->weyl_on ? 0x9E3779B9u : 0u,
                             s) != cudaSuccess)
         return XG_ECUDA;
-    for (size_t b = 0; b < lists.size(); ++b) {
-        if (lists[b].empty()) continue;
-        if (launch_gf2_apply_listed(mats[b], reinterpret_cast<uint64_t*>(db + off_rings), (uint32_t)lists[b].size(),
-                                    reinterpret_cast<const uint32_t*>(db + list_off[b]),
-                                    reinterpret_cast<uint64_t*>(db + off_tmp), c->sm_count, s) != cudaSuccess)
+    for (size_t b = 0; b < src.size(); ++b) {
+        if (src[b].empty()) continue;
+        if (zero_rings(reinterpret_cast<uint32_t*>(db + off_rings), reinterpret_cast<const uint32_t*>(db + dst_off[b]),
+                       (uint32_t)dst[b].size(), s) != cudaSuccess)
+            return XG_ECUDA;
+        if (launch_gf2_apply_pairs(mats[b], reinterpret_cast<uint32_t*>(db + off_rings), (uint32_t)src[b].size(),
+                                   reinterpret_cast<const uint32_t*>(db + src_off[b]),
+                                   reinterpret_cast<const uint32_t*>(db + dst_off[b]), c->sm_count, s) != cudaSuccess)
             return XG_ECUDA;
     }
     return XG_OK;
@@ -268,7 +289,7 @@ xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cu
         if (xg_status st = reserve(c, std::max<uint32_t>(n, 64))) return st;
     }
     if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
-    plan_batch(items, n, choose_piece_len(c, items, n), plan_);
+    plan_batch(items, n, choose_piece_len(c, items, n), c->n, plan_);
     const uint32_t nu = (uint32_t)plan_.units.size();
     if (xg_status st = reserve(c, nu)) return st;
     if (xg_status st = prologue(c, s)) return st;

@@ -33,12 +33,14 @@ struct BatchPlan {
     std::vector<uint32_t> piece_index;   // m: the piece starts m * 2^split_log2 words in
     std::vector<uint32_t> units_per_item;
     int split_log2 = 0;                  // piece length 2^split_log2 (when pieces exist)
+    // dense per-stream scratch, all zero between calls
+    std::vector<uint32_t> items_of_stream, last_unit, chain_of;
 };
 
 // Plan a batch.  piece_len: 0 = cut nothing, else a power of two; calls alone
 // on their stream with at least 2 * piece_len words are cut into pieces of
 // piece_len words (the last one shorter).
-void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, BatchPlan& plan);
+void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan);
 
 class BatchLauncher {
 public:

@@ -131,6 +131,60 @@ __global__ void __launch_bounds__(64) gf2_apply_partial_kernel(const uint64_t* _
                       (unsigned long long)acc[v]);
 }
 
+// dst[i] ^= C src[i] for n (src, dst) pairs, dst zeroed beforehand.  Block
+// (x, y): pairs [8x, 8x+8), columns [y*cols, (y+1)*cols); 128 threads, thread
+// t owns 32-bit word t of every result and folds its partial XOR into dst
+// with one atomic XOR per pair.
+constexpr int kPairVecs = 8;
+__global__ void __launch_bounds__(128) gf2_apply_pairs_kernel(const uint32_t* __restrict__ C,
+                                                              const uint32_t* __restrict__ rings,
+                                                              const uint32_t* __restrict__ src,
+                                                              const uint32_t* __restrict__ dst, uint32_t n,
+                                                              uint32_t* __restrict__ out, int cols)
+{
+    __shared__ uint32_t vbits[kPairVecs][kR];
+    const int t = threadIdx.x;
+    const uint32_t base = blockIdx.x * kPairVecs;
+    const int nv = (int)umin((uint32_t)kPairVecs, n - base);
+    for (int v = 0; v < kPairVecs; ++v)
+        vbits[v][t] = v < nv ? rings[(size_t)src[base + v] * kR + t] : 0u;
+    __syncthreads();
+    uint32_t acc[kPairVecs];
+#pragma unroll
+    for (int v = 0; v < kPairVecs; ++v) acc[v] = 0;
+    const int w0 = blockIdx.y * (cols / 32), w1 = w0 + cols / 32;
+    for (int w = w0; w < w1; ++w) {  // 32 columns per input word
+        uint32_t bw[kPairVecs];
+        uint32_t any = 0;
+#pragma unroll
+        for (int v = 0; v < kPairVecs; ++v) {
+            bw[v] = vbits[v][w];
+            any |= bw[v];
+        }
+        if (!any) continue;
+        const uint32_t* colw = C + (size_t)w * 32 * kR + t;
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b) {
+            if (!((any >> b) & 1u)) continue;
+            const uint32_t col = colw[(size_t)b * kR];
+#pragma unroll
+            for (int v = 0; v < kPairVecs; ++v) {
+                const uint32_t m = (uint32_t)((int32_t)(bw[v] << (31 - b)) >> 31);
+                acc[v] ^= col & m;
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kPairVecs; ++v)
+        if (v < nv && acc[v]) atomicXor(&out[(size_t)dst[base + v] * kR + t], acc[v]);
+}
+
+__global__ void zero_listed_kernel(uint32_t* __restrict__ rings, const uint32_t* __restrict__ idx, uint32_t n)
+{
+    const uint32_t j = blockIdx.x;
+    if (j < n) rings[(size_t)idx[j] * kR + threadIdx.x] = 0u;
+}
+
 __global__ void copy_listed_kernel(const uint64_t* __restrict__ tmp, uint64_t* __restrict__ vecs,
                                    const uint32_t* __restrict__ idx, uint32_t n)
 {
@@ -244,6 +298,26 @@ cudaError_t launch_gf2_apply_listed(const uint64_t* C, uint64_t* vecs, uint32_t 
     if (e != cudaSuccess) return e;
     gf2_apply_partial_kernel<<<dim3(groups, chunks), 64, 0, s>>>(C, vecs, d_idx, n, d_tmp, 64 / chunks);
     copy_listed_kernel<<<n, 64, 0, s>>>(d_tmp, vecs, d_idx, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gf2_apply_pairs(const uint64_t* C, uint32_t* rings, uint32_t n, const uint32_t* d_src,
+                                   const uint32_t* d_dst, int sm_count, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint32_t groups = (n + kPairVecs - 1) / kPairVecs;
+    // enough blocks for about 8 per SM, splitting the 4096 columns if needed
+    int chunks = 1;
+    while (chunks < 32 && (uint64_t)groups * chunks < (uint64_t)8 * sm_count) chunks *= 2;
+    gf2_apply_pairs_kernel<<<dim3(groups, chunks), 128, 0, s>>>(reinterpret_cast<const uint32_t*>(C), rings, d_src,
+                                                               d_dst, n, rings, kBits / chunks);
+    return cudaGetLastError();
+}
+
+cudaError_t zero_rings(uint32_t* rings, const uint32_t* d_idx, uint32_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    zero_listed_kernel<<<n, kR, 0, s>>>(rings, d_idx, n);
     return cudaGetLastError();
 }
 

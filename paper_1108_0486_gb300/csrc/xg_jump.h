@@ -24,6 +24,14 @@ cudaError_t launch_gf2_apply(const uint64_t* C, uint64_t* vecs, uint32_t n, cons
 cudaError_t launch_gf2_apply_listed(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx,
                                     uint64_t* d_tmp, int sm_count, cudaStream_t s);
 
+// rings[d_dst[i]] ^= C rings[d_src[i]] for n pairs (destinations distinct,
+// not among the sources, zeroed beforehand); rings are 128-word states.
+cudaError_t launch_gf2_apply_pairs(const uint64_t* C, uint32_t* rings, uint32_t n, const uint32_t* d_src,
+                                   const uint32_t* d_dst, int sm_count, cudaStream_t s);
+
+// rings[d_idx[i]] = 0 for n listed 128-word rings.
+cudaError_t zero_rings(uint32_t* rings, const uint32_t* d_idx, uint32_t n, cudaStream_t s);
+
 // rings[k] = current ring of stream d_streams[k]; weyl0[k * weyl0_stride] =
 // its Weyl word advanced by d_skip[k] words (weyl0 may be null).
 cudaError_t launch_gather_rings(const State& st, const uint32_t* d_streams, uint32_t n, uint32_t* d_rings,

@@ -14,6 +14,7 @@
 //   complete-> the kernel fences each request's stores and sets its flag in
 //              mapped pinned host memory; xg_poll reads it directly.
 #include <atomic>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -145,6 +146,9 @@ public:
                 return fail(XG_ECUDA, "server: stream creation failed");
             if (xg_status s = l.launcher->reserve(c_, cfg_.max_batch)) return fail(s, "server: batch launcher");
         }
+        // host-side fault injection for tests: the first N batch launches
+        // report failure without reaching the GPU
+        if (const char* f = std::getenv("XG_INJECT_LAUNCH_FAILURES")) inject_failures_ = std::atoi(f);
         run_ = true;
         th_ = std::thread([this] { loop(); });
         return XG_OK;
@@ -283,6 +287,41 @@ public:
         return XG_OK;
     }
 
+    // Up to max finished tickets, oldest completion first; optionally
+    // released as well.
+    xg_status collect(xg_completion* out, uint32_t max, uint32_t* n_out, int release)
+    {
+        uint32_t n = 0;
+        std::lock_guard<std::mutex> lk(mu_);
+        while (n < max) {
+            std::shared_ptr<Ticket> t;
+            {
+                std::lock_guard<std::mutex> dl(done_mu_);
+                if (done_q_.empty()) break;
+                t = done_q_.front();
+                done_q_.pop_front();
+            }
+            auto it = tickets_.find(t->id);
+            if (it == tickets_.end()) continue;  // already released by its owner
+            xg_completion& c = out[n++];
+            c.ticket = t->id;
+            c.t_submit_ns = t->t_submit;
+            c.t_launch_ns = t->t_launch;
+            c.t_done_ns = t->t_done.load();
+            c.status = t->state.load() == kDone ? XG_OK : XG_EDEVICE;
+            c.pad = 0;
+            c.d_result = t->out;
+            if (release) {
+                if (t->pooled) pool_.release(t->out);
+                outstanding_ -= t->bytes;
+                tickets_.erase(it);
+                c.d_result = nullptr;
+            }
+        }
+        *n_out = n;
+        return XG_OK;
+    }
+
     void stats(xg_server_stats* s)
     {
         std::lock_guard<std::mutex> lk(mu_);
@@ -385,8 +424,9 @@ private:
                 if (items.empty()) continue;
                 in_flight_ += items.size();
                 units.resize(items.size());
-                const xg_status lst = l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream,
-                                                         units.data());
+                xg_status lst = XG_ECUDA;
+                if (inject_failures_ > 0) --inject_failures_;
+                else lst = l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream, units.data());
                 for (size_t j = 0; j < l.inflight.size(); ++j) {
                     l.inflight[j]->expected = lst == XG_OK ? units[j] : 1u;
                     l.inflight[j]->state.store(kRunning, std::memory_order_release);
@@ -429,6 +469,8 @@ private:
         if (it != fifo_.end() && !it->second.empty()) ready_.push({it->second.front()->seq, s});
         ++completed_;
         --in_flight_;
+        std::lock_guard<std::mutex> dl(done_mu_);
+        done_q_.push_back(t);
     }
 
     xg_ctx* c_;
@@ -443,6 +485,9 @@ private:
     uint64_t submitted_ = 0, refused_ = 0;
     std::atomic<uint64_t> completed_{0}, batches_{0}, items_launched_{0}, queued_{0}, in_flight_{0};
     std::atomic<bool> launch_error_{false};
+    int inject_failures_ = 0;
+    std::mutex done_mu_;
+    std::deque<std::shared_ptr<Ticket>> done_q_;  // finished, not yet collected
     // scheduler thread only
     std::unordered_map<uint32_t, std::deque<std::shared_ptr<Ticket>>> fifo_;
     std::unordered_set<uint32_t> busy_streams_;
@@ -532,6 +577,13 @@ xg_status xg_ticket_times(xg_ctx* ctx, uint64_t ticket, uint64_t* t_submit_ns, u
     if (!ctx) return fail(XG_EINVAL, "null context");
     if (!ctx->server) return fail(XG_EINVAL, "server not running");
     return ctx->server->times(ticket, t_submit_ns, t_launch_ns, t_done_ns);
+}
+
+xg_status xg_collect(xg_ctx* ctx, xg_completion* out, uint32_t max, uint32_t* n_out, int release)
+{
+    if (!ctx || !n_out || (max && !out)) return fail(XG_EINVAL, "null argument");
+    if (!ctx->server) return fail(XG_EINVAL, "server not running");
+    return ctx->server->collect(out, max, n_out, release);
 }
 
 xg_status xg_server_stats_get(xg_ctx* ctx, xg_server_stats* out)

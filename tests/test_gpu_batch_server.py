@@ -323,3 +323,52 @@ def test_server_with_cut_requests():
     refs = oracle_per_item(seeds, reqs)
     for (s, k, n), o, ref in zip(reqs, outs, refs):
         check(k, o[:n], ref)
+
+
+# ------------------------------------------------- failure detection (host)
+
+def test_server_survives_failed_launches(monkeypatch):
+    """Host-side fault injection: the first two batch launches fail before
+    reaching the GPU.  Their requests report XG_EDEVICE, leave their streams
+    untouched, and the server goes on serving."""
+    from paper_1108_0486_gb300 import XGError, _lib as L
+    monkeypatch.setenv("XG_INJECT_LAUNCH_FAILURES", "2")
+    seeds = W.seeds(3)
+    outs = [alloc("u32", 1000) for _ in range(4)]
+    with Streams(3, seeds=seeds) as st:
+        srv = st.serve(lanes=1, max_batch=1)
+        failed = 0
+        for i in range(2):
+            t = srv.submit(i, "u32", 1000, out=outs[i])
+            with pytest.raises(XGError) as e:
+                srv.wait(t, 10000)
+            assert e.value.status == L.XG_EDEVICE
+            srv.release(t)
+            failed += 1
+        t = srv.submit(0, "u32", 1000, out=outs[2])
+        srv.wait(t, 10000)
+        t2 = srv.submit(0, "u32", 1000, out=outs[3])
+        srv.wait(t2, 10000)
+        srv.stop()
+    assert failed == 2
+    ref = O.Xorgens.param_set(0).seed(int(seeds[0])).u32(2000)
+    assert np.array_equal(outs[2].cpu().numpy().view(np.uint32), ref[:1000])
+    assert np.array_equal(outs[3].cpu().numpy().view(np.uint32), ref[1000:])
+
+
+def test_collect_drains_finished_requests():
+    seeds = W.seeds(16)
+    with Streams(16, seeds=seeds) as st:
+        srv = st.serve()
+        tickets = {srv.submit(i, KINDS[i % 3], 5000 + i) for i in range(16)}
+        got = []
+        for _ in range(2000):
+            got += srv.collect(release=True)
+            if len(got) == 16:
+                break
+            import time
+            time.sleep(0.001)
+        assert {g[0] for g in got} == tickets and all(g[4] == 0 for g in got)
+        assert all(g[1] <= g[2] <= g[3] for g in got)  # submit <= launch <= done
+        assert srv.stats()["outstanding_bytes"] == 0
+        srv.stop()
