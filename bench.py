@@ -399,7 +399,8 @@ def batched_row(torch, L, stream, peak, reps=3):
             "hbm_floor_ms": total * 4 / peak / 1e6}
 
 
-def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0):
+def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0, lanes=48, split=0,
+                plain=True):
     """Open-loop Poisson arrivals at `rate` req/s on 65536 resident streams,
     sizes log-uniform in [2^10, 2^22], 60/30/10 normal/uniform/u32, memory
     cap 16 GiB (library pool).  Latency = completion seen by the host minus
@@ -411,7 +412,9 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0)
     reqs = W.serving_requests(n_streams=S, rate=rate, duration=seconds)
     st = Streams(S, seeds=W.seeds(S), stream=stream)
     torch.cuda.synchronize()
-    L.xg_server_start(st.ctx, 16 << 30, 1024, 16)
+    if split:
+        st.set_batch_split(split)
+    L.xg_server_start(st.ctx, 16 << 30, 1024, lanes)
     done_times = []
     refused = [0]
     n_total = len(reqs)
@@ -462,7 +465,11 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0)
            "max_ms": float(lat.max()), "p50_queue_ms": float(np.percentile(qwait, 50)),
            "p99_queue_ms": float(np.percentile(qwait, 99)), "refused_retries": refused[0],
            "batches": stats["batches"], "mean_batch": stats["items_launched"] / max(1, stats["batches"]),
-           "wall_s": wall}
+           "server_thread_launch_busy": stats["host_launch_ns"] / 1e9 / wall, "wall_s": wall,
+           "lanes": lanes, "piece_words": split or "auto"}
+    if not plain:
+        st.close()
+        return row
     # plain path: one launch per request, in arrival order, on one CUDA stream
     preqs = [r for r in reqs if r.t_arrival < plain_seconds]
     buf = torch.empty(1 << 22, dtype=torch.int32, device="cuda")
@@ -545,6 +552,41 @@ def end_to_end(st, stream, torch, L, args):
             "note": "host buffers are pinned; no inputs cross per step (state resident)"}
 
 
+def profile_kernel(args):
+    """One kernel's workload alone, for ncu captures (prints a JSON line
+    marked as a profiling case; not a bench line).  --n-per sets the words
+    per stream (16384 streams), or the batch's length cap."""
+    import torch
+    from paper_1108_0486_gb300 import Streams, _lib as L
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n = args.n_per or N_PER
+    out = {"profiling_case": args.kernel, "n_per": n}
+    if args.kernel in ("normal", "normal_sum", "u32", "uniform"):
+        st = Streams(STREAMS, seeds=W.seeds(STREAMS), stream=stream)
+        kind = "normal" if args.kernel.startswith("normal") else args.kernel
+        if not args.no_autotune:
+            out["launch"] = st.autotune(kind, n)
+        if args.kernel == "normal_sum":
+            sums = torch.empty(STREAMS, dtype=torch.float32, device="cuda")
+            fn = lambda: st.normal_sum(n, out=sums)
+        else:
+            buf = torch.empty((STREAMS, n), dtype=torch.int32 if kind == "u32" else torch.float32,
+                              device="cuda")
+            fn = lambda: st.generate(kind, n, out=buf)
+        out["ms"] = _time(fn, stream, torch, reps=args.steps, warm=args.warmup)
+    elif args.kernel == "batch":
+        items = [it for it in W.batched_uneven() if it.count <= n] if args.n_per else W.batched_uneven()
+        st = Streams(4096, seeds=W.seeds(4096), stream=stream)
+        outs = [torch.empty(it.count, dtype=torch.int32, device="cuda") for it in items]
+        arr = L.make_items([(it.stream, it.kind, it.count, o.data_ptr()) for it, o in zip(items, outs)])
+        out["items"] = len(items)
+        out["ms"] = _time(lambda: L.xg_generate_batch(st.ctx, arr), stream, torch, reps=args.steps,
+                          warm=args.warmup)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -557,6 +599,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="arrival window of the serving row (10 s for the full 200K requests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default=None, choices=["u32", "uniform", "normal", "normal_sum", "batch"],
+                    help="time one kernel's workload alone (profiling case; not a bench line)")
     ap.add_argument("--n-per", type=int, default=None,
                     help="override words per stream (profiling of a smaller case; not a bench line)")
     ap.add_argument("--traffic", type=float, default=None,
@@ -569,7 +613,9 @@ def main():
         N_PER = args.n_per
         CONFIG["n_per_stream"] = N_PER
         CONFIG["workload"] = f"PROFILING CASE: {STREAMS} streams x {N_PER} words (not the bench workload)"
-    if args.impl == "reference":
+    if args.kernel:
+        profile_kernel(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

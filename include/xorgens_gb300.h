@@ -207,7 +207,7 @@ typedef struct {
                                one device allocation of this size. */
     uint32_t max_batch;     /* requests per batch launch; 0 = 1024 */
     uint32_t lanes;         /* batches in flight at once, each on its own CUDA
-                               stream; 0 = 16, at most 64 */
+                               stream; 0 = 48, at most 64 */
 } xg_server_config;
 
 typedef struct {
@@ -222,6 +222,7 @@ typedef struct {
     uint64_t submitted, completed, refused, queued, in_flight, batches, items_launched;
     uint64_t outstanding_bytes;
     uint64_t now_ns; /* the server clock (steady, ns) that xg_ticket_times uses */
+    uint64_t host_launch_ns; /* host time the server thread spent launching batches */
 } xg_server_stats;
 
 /* Start the request server on a context.  From then on the context's streams

@@ -56,7 +56,7 @@ class XgCompletion(ctypes.Structure):
 class XgServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "submitted", "completed", "refused", "queued", "in_flight", "batches", "items_launched",
-        "outstanding_bytes", "now_ns")]
+        "outstanding_bytes", "now_ns", "host_launch_ns")]
 
 
 # name -> argtypes (all return xg_status unless listed in _RESTYPES)

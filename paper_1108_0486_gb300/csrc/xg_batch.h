@@ -25,8 +25,8 @@ struct HostItem {
 
 struct BatchPlan {
     std::vector<BatchItem> units;        // device items (whole calls and pieces)
-    std::vector<uint32_t> heads;         // chain heads, longest chain first
-    std::vector<uint64_t> chain_words;   // words per chain, same order
+    std::vector<uint32_t> heads;         // chain heads, costliest chain first
+    std::vector<uint64_t> chain_words;   // estimated cost per chain, same order
     std::vector<BatchPiece> pieces;      // ring/weyl pointers filled at launch
     std::vector<uint32_t> piece_stream;  // stream of each piece
     std::vector<uint64_t> piece_skip;    // words of its call before each piece

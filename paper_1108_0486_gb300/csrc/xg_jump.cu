@@ -154,23 +154,18 @@ __global__ void __launch_bounds__(128) gf2_apply_pairs_kernel(const uint32_t* __
     for (int v = 0; v < kPairVecs; ++v) acc[v] = 0;
     const int w0 = blockIdx.y * (cols / 32), w1 = w0 + cols / 32;
     for (int w = w0; w < w1; ++w) {  // 32 columns per input word
-        uint32_t bw[kPairVecs];
-        uint32_t any = 0;
+        // all 32 column words first (independent loads in flight together)
+        const uint32_t* colw = C + (size_t)w * 32 * kR + t;
+        uint32_t col[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) col[b] = __ldg(colw + (size_t)b * kR);
 #pragma unroll
         for (int v = 0; v < kPairVecs; ++v) {
-            bw[v] = vbits[v][w];
-            any |= bw[v];
-        }
-        if (!any) continue;
-        const uint32_t* colw = C + (size_t)w * 32 * kR + t;
-#pragma unroll 8
-        for (int b = 0; b < 32; ++b) {
-            if (!((any >> b) & 1u)) continue;
-            const uint32_t col = colw[(size_t)b * kR];
+            const uint32_t bw = vbits[v][w];
 #pragma unroll
-            for (int v = 0; v < kPairVecs; ++v) {
-                const uint32_t m = (uint32_t)((int32_t)(bw[v] << (31 - b)) >> 31);
-                acc[v] ^= col & m;
+            for (int b = 0; b < 32; ++b) {
+                const uint32_t m = (uint32_t)((int32_t)(bw << (31 - b)) >> 31);
+                acc[v] ^= col[b] & m;
             }
         }
     }

@@ -130,7 +130,7 @@ public:
         cfg_ = cfg;
         if (cfg_.mem_cap_bytes == 0) cfg_.mem_cap_bytes = size_t(16) << 30;
         if (cfg_.max_batch == 0) cfg_.max_batch = 1024;
-        if (cfg_.lanes == 0) cfg_.lanes = 16;
+        if (cfg_.lanes == 0) cfg_.lanes = 48;
         if (cfg_.lanes > 64) return fail(XG_EINVAL, "at most 64 lanes");
         if (xg_status s = pool_.init(cfg_.mem_cap_bytes)) return s;
         const size_t nflags = (size_t)cfg_.lanes * cfg_.max_batch;
@@ -334,6 +334,7 @@ public:
         s->queued = queued_.load();
         s->in_flight = in_flight_.load();
         s->now_ns = now_ns();
+        s->host_launch_ns = launch_ns_.load();
     }
 
 private:
@@ -426,7 +427,11 @@ private:
                 units.resize(items.size());
                 xg_status lst = XG_ECUDA;
                 if (inject_failures_ > 0) --inject_failures_;
-                else lst = l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream, units.data());
+                else {
+                    const uint64_t h0 = now_ns();
+                    lst = l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream, units.data());
+                    launch_ns_ += now_ns() - h0;
+                }
                 for (size_t j = 0; j < l.inflight.size(); ++j) {
                     l.inflight[j]->expected = lst == XG_OK ? units[j] : 1u;
                     l.inflight[j]->state.store(kRunning, std::memory_order_release);
@@ -484,6 +489,7 @@ private:
     size_t outstanding_ = 0;
     uint64_t submitted_ = 0, refused_ = 0;
     std::atomic<uint64_t> completed_{0}, batches_{0}, items_launched_{0}, queued_{0}, in_flight_{0};
+    std::atomic<uint64_t> launch_ns_{0};
     std::atomic<bool> launch_error_{false};
     int inject_failures_ = 0;
     std::mutex done_mu_;
