@@ -289,12 +289,24 @@ __global__ void __launch_bounds__(256) seed_kernel(State st, const uint32_t* __r
     }
 }
 
-// One call on one stream s: n outputs of kind OUT written to row (this
-// stream's first output), the stream state read at the start and written
-// back at the end.  Returns the lane's partial sum for kNormalSum.
+// Where a call's words start from.  A whole call reads the stream's ring
+// from its window and writes the stream state back; a piece of a cut call
+// reads the ring and Weyl word the jump prologue prepared, and only the last
+// piece writes the state back (adding the whole call's words to pos).
+struct UnitSrc {
+    const uint32_t* ring = nullptr;   // null: the stream's window
+    const uint32_t* weyl0 = nullptr;  // with ring: Weyl word before the first word
+    uint64_t pos_add = 0;             // with ring: words the whole call advances
+    bool write_state = true;
+};
+
+// One call (or piece) on one stream s: n outputs of kind OUT written to row
+// (this stream's first output).  Returns the lane's partial sum for
+// kNormalSum.
 template <class P, int TPG, int WPL, int OUT, bool VEC>
 __device__ __forceinline__ float run_stream(const State& st, uint32_t s, uint64_t n, uint32_t* row,
-                                            uint32_t omega, int lane, unsigned mask)
+                                            uint32_t omega, int lane, unsigned mask,
+                                            const UnitSrc& src = UnitSrc())
 {
     using E = Engine<P, TPG, WPL>;
     constexpr int RW = E::RW;
@@ -307,9 +319,14 @@ __device__ __forceinline__ float run_stream(const State& st, uint32_t s, uint64_
     eng.lane = lane;
     eng.mask = mask;
     uint32_t* win_s = st.win + (uint64_t)s * kWin;
-    const uint32_t pend = st.pend[s];
-    const uint32_t wp = st.weyl[s];
-    load_ring(eng, win_s, pend);
+    uint32_t wp;
+    if (src.ring) {
+        load_ring(eng, src.ring - kRingBase, 0u);
+        wp = *src.weyl0;
+    } else {
+        load_ring(eng, win_s, st.pend[s]);
+        wp = st.weyl[s];
+    }
     em.omega = omega;
     em.limit = n;
     em.lane_off = (uint64_t)WPL * lane;
@@ -318,52 +335,16 @@ __device__ __forceinline__ float run_stream(const State& st, uint32_t s, uint64_
     uint32_t retired[WPL];
     const uint64_t nr = (nwords + RW - 1) / RW;
     const int rot = drive(eng, nr, em, retired);
-    __syncwarp(mask);
-    store_window(eng, win_s, rot, retired);
-    if (lane == 0) {
-        st.weyl[s] = wp + (uint32_t)nwords * omega;
-        st.pend[s] = (uint32_t)(nr * RW - nwords);
-        st.pos[s] += nwords;
-    }
-    return em.acc;
-}
-
-// One piece of a split call (32 lanes, 64-word rounds): the start ring and
-// Weyl word come from the piece table; only the last piece writes the stream
-// state back, as the whole call would have left it.
-template <class P, int OUT, bool VEC>
-__device__ __forceinline__ void run_piece(const State& st, uint32_t s, uint64_t n, uint32_t* row,
-                                          uint32_t omega, int lane, const BatchPiece& pc)
-{
-    using E = Engine<P, 32, 2>;
-    constexpr int RW = E::RW;
-    constexpr bool kNormalOut = (OUT == kNormal);
-    const uint64_t nwords = kNormalOut ? n + (n & 1u) : n;
-    if (nwords == 0) return;
-    Emit<E, OUT, VEC> em;
-    em.acc = 0.0f;
-    E eng;
-    eng.lane = lane;
-    eng.mask = 0xFFFFFFFFu;
-    load_ring(eng, pc.ring - kRingBase, 0u);
-    const uint32_t wp = *pc.weyl0;
-    em.omega = omega;
-    em.limit = n;
-    em.lane_off = (uint64_t)2 * lane;
-    em.wl = wp + (uint32_t)(2 * lane + 1) * omega;
-    em.dst = row + em.lane_off;
-    uint32_t retired[2];
-    const uint64_t nr = (nwords + RW - 1) / RW;
-    const int rot = drive(eng, nr, em, retired);
-    if (pc.last) {
-        __syncwarp();
-        store_window(eng, st.win + (uint64_t)s * kWin, rot, retired);
+    if (src.write_state) {
+        __syncwarp(mask);
+        store_window(eng, win_s, rot, retired);
         if (lane == 0) {
             st.weyl[s] = wp + (uint32_t)nwords * omega;
             st.pend[s] = (uint32_t)(nr * RW - nwords);
-            st.pos[s] += pc.item_words;
+            st.pos[s] += src.ring ? src.pos_add : nwords;
         }
     }
+    return em.acc;
 }
 
 template <class P, int TPG, int WPL, int OUT, bool VEC>
@@ -398,36 +379,26 @@ __device__ __forceinline__ void run_item(const State& st, const BatchItem& it, c
     uint32_t* row = reinterpret_cast<uint32_t*>(it.out);
     const bool vec = (reinterpret_cast<uintptr_t>(row) & 15u) == 0;
     constexpr unsigned kFull = 0xFFFFFFFFu;
+    UnitSrc src;
     if (it.piece) {
-        const BatchPiece pc = pieces[it.piece - 1];
-        switch (it.kind) {
-        case kU32:
-            if (vec) run_piece<P, kU32, true>(st, it.stream, it.count, row, omega, lane, pc);
-            else run_piece<P, kU32, false>(st, it.stream, it.count, row, omega, lane, pc);
-            break;
-        case kUniform:
-            if (vec) run_piece<P, kUniform, true>(st, it.stream, it.count, row, omega, lane, pc);
-            else run_piece<P, kUniform, false>(st, it.stream, it.count, row, omega, lane, pc);
-            break;
-        default:
-            if (vec) run_piece<P, kNormal, true>(st, it.stream, it.count, row, omega, lane, pc);
-            else run_piece<P, kNormal, false>(st, it.stream, it.count, row, omega, lane, pc);
-            break;
-        }
-        return;
+        const BatchPiece& pc = pieces[it.piece - 1];
+        src.ring = pc.ring;
+        src.weyl0 = pc.weyl0;
+        src.pos_add = pc.item_words;
+        src.write_state = pc.last != 0;
     }
     switch (it.kind) {
     case kU32:
-        if (vec) run_stream<P, 32, 2, kU32, true>(st, it.stream, it.count, row, omega, lane, kFull);
-        else run_stream<P, 32, 2, kU32, false>(st, it.stream, it.count, row, omega, lane, kFull);
+        if (vec) run_stream<P, 32, 2, kU32, true>(st, it.stream, it.count, row, omega, lane, kFull, src);
+        else run_stream<P, 32, 2, kU32, false>(st, it.stream, it.count, row, omega, lane, kFull, src);
         break;
     case kUniform:
-        if (vec) run_stream<P, 32, 2, kUniform, true>(st, it.stream, it.count, row, omega, lane, kFull);
-        else run_stream<P, 32, 2, kUniform, false>(st, it.stream, it.count, row, omega, lane, kFull);
+        if (vec) run_stream<P, 32, 2, kUniform, true>(st, it.stream, it.count, row, omega, lane, kFull, src);
+        else run_stream<P, 32, 2, kUniform, false>(st, it.stream, it.count, row, omega, lane, kFull, src);
         break;
     default:
-        if (vec) run_stream<P, 32, 2, kNormal, true>(st, it.stream, it.count, row, omega, lane, kFull);
-        else run_stream<P, 32, 2, kNormal, false>(st, it.stream, it.count, row, omega, lane, kFull);
+        if (vec) run_stream<P, 32, 2, kNormal, true>(st, it.stream, it.count, row, omega, lane, kFull, src);
+        else run_stream<P, 32, 2, kNormal, false>(st, it.stream, it.count, row, omega, lane, kFull, src);
         break;
     }
 }
