@@ -234,7 +234,9 @@ typedef struct {
  * (one replay of the persistent batch kernel's graph).  Batches on different
  * lanes run concurrently, so requests that arrive while others are on the
  * GPU start as soon as a lane and memory free up.  Each result is identical
- * to the same request run alone.  A request whose batch fails to launch is
+ * to the same request run alone.  Start-up allocates the pool, each lane's
+ * buffers and the jump-ahead powers (about 70 MiB) so that serving itself
+ * does not allocate.  A request whose batch fails to launch is
  * reported as XG_EDEVICE by xg_poll / xg_wait and leaves its stream where it
  * was; the server keeps serving.  (For testing that path without a GPU
  * fault, the environment variable XG_INJECT_LAUNCH_FAILURES=N, read at

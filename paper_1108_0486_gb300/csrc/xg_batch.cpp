@@ -194,6 +194,27 @@ uint64_t BatchLauncher::choose_piece_len(const xg_ctx* c, const HostItem* items,
     return longest >= 2 * len ? len : 0;
 }
 
+xg_status BatchLauncher::grow_jump(size_t want)
+{
+    if (want <= jbytes_) return XG_OK;
+    if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
+    if (h_jstage_) cudaFreeHost(h_jstage_);
+    if (d_jbuf_) cudaFree(d_jbuf_);
+    h_jstage_ = nullptr;
+    d_jbuf_ = nullptr;
+    jbytes_ = 0;
+    if (cudaHostAlloc(&h_jstage_, want, cudaHostAllocDefault) != cudaSuccess) return XG_ENOMEM;
+    if (cudaMalloc(&d_jbuf_, want) != cudaSuccess) return XG_ENOMEM;
+    jbytes_ = want;
+    return XG_OK;
+}
+
+xg_status BatchLauncher::reserve_jump(uint32_t pieces, uint32_t pairs)
+{
+    // the layout of prologue(): rings, weyls, streams, skips, pair lists
+    return grow_jump((size_t)pieces * (512 + 4 + 4 + 8 + 64) + (size_t)pairs * 8 + 4096);
+}
+
 // Start rings of the pieces.  Piece 0 of a call gets the stream's ring
 // (gather).  Then, doubling: step b gives every piece m in [2^b, 2^(b+1)) the
 // ring of piece m - 2^b advanced by 2^b pieces, i.e. C_{q+b} applied to it
@@ -227,16 +248,7 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
     const size_t off_lists = off_skip + (size_t)P * 8;
     const size_t total = off_lists + 2 * npairs * 4 + 16;
     if (total > jbytes_) {
-        if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
-        if (h_jstage_) cudaFreeHost(h_jstage_);
-        if (d_jbuf_) cudaFree(d_jbuf_);
-        h_jstage_ = nullptr;
-        d_jbuf_ = nullptr;
-        jbytes_ = 0;
-        const size_t want = total + total / 2;
-        if (cudaHostAlloc(&h_jstage_, want, cudaHostAllocDefault) != cudaSuccess) return XG_ENOMEM;
-        if (cudaMalloc(&d_jbuf_, want) != cudaSuccess) return XG_ENOMEM;
-        jbytes_ = want;
+        if (xg_status st = grow_jump(total + total / 2)) return st;
     }
     char* hb = static_cast<char*>(h_jstage_);
     char* db = static_cast<char*>(d_jbuf_);

@@ -53,6 +53,9 @@ public:
     // receives how many completion increments each item will produce.
     xg_status launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s,
                      uint32_t* units_per_item = nullptr);
+    // Preallocate the jump prologue's buffers for up to `pieces` pieces (so
+    // that a later launch does not allocate).
+    xg_status reserve_jump(uint32_t pieces, uint32_t pairs);
     size_t scratch_bytes() const { return bytes_; }
     cudaEvent_t done_event() const { return done_; }
     bool busy() const;
@@ -60,6 +63,7 @@ public:
 private:
     xg_status build_graph(xg_ctx* c);
     xg_status prologue(xg_ctx* c, cudaStream_t s);
+    xg_status grow_jump(size_t want);
     uint64_t choose_piece_len(const xg_ctx* c, const HostItem* items, uint32_t n) const;
     uint32_t capacity_ = 0;
     size_t bytes_ = 0;

@@ -113,12 +113,12 @@ __device__ __forceinline__ void normal_pair(uint32_t o1, uint32_t o2, float& z1,
         return;
     }
     const float R = sqrt_refined(neg2ln_u1(m1));
-    // angle 2 pi u2 = n (pi/2) + (pi/4) x, reduced exactly in integers
-    const uint32_t q = (m2 + (1u << 21)) >> 22;                  // 0..4
-    const int rr = (int)m2 - (int)(q << 22);                     // [-2^21, 2^21)
+    // angle 2 pi u2 = n (pi/2) + (pi/4) x with n = q mod 4, reduced exactly in
+    // integers: mm = m2 + 2^21 holds q = mm >> 22 and x 2^21 = (mm mod 2^22) - 2^21
+    const uint32_t mm = m2 + (1u << 21);
+    const int rr = (int)(mm & 0x3FFFFFu) - (1 << 21);            // [-2^21, 2^21)
     const float x = __fmul_rn(__int2float_rn(rr), 0x1p-21f);     // exact
     const float y = __fmul_rn(x, x);
-    const float ylo = __fmaf_rn(x, x, -y);                       // x^2 = y + ylo exactly
     float sp = kSinS[3];
     sp = __fmaf_rn(sp, y, kSinS[2]);
     sp = __fmaf_rn(sp, y, kSinS[1]);
@@ -127,13 +127,15 @@ __device__ __forceinline__ void normal_pair(uint32_t o1, uint32_t o2, float& z1,
     cp = __fmaf_rn(cp, y, kCosC[2]);
     cp = __fmaf_rn(cp, y, kCosC[1]);
     cp = __fmaf_rn(cp, y, kCosC[0]);
-    const float c = __fmaf_rn(cp, y, __fmaf_rn(cp, ylo, 1.0f));
-    // quadrant n = q mod 4: (cos, sin) = (c,s), (-s,c), (-c,-s), (s,-c)
-    const uint32_t n = q & 3u;
-    const float cs = (n & 1u) ? s : c;
-    const float sn = (n & 1u) ? c : s;
-    const uint32_t cflip = ((n + 1u) & 2u) << 30;
-    const uint32_t sflip = (n & 2u) << 30;
+    const float c = __fmaf_rn(cp, y, 1.0f);
+    // (cos, sin) = (c,s), (-s,c), (-c,-s), (s,-c) for n = 0..3: swap when n is
+    // odd (bit 22 of mm); the first is negated when bit 1 of n + 1 is set
+    // (bit 23 of mm + 2^22), the second when bit 1 of n is (bit 23 of mm)
+    const bool odd = (mm >> 22) & 1u;
+    const float cs = odd ? s : c;
+    const float sn = odd ? c : s;
+    const uint32_t cflip = ((mm + (1u << 22)) << 8) & 0x80000000u;
+    const uint32_t sflip = (mm << 8) & 0x80000000u;
     z1 = __fmul_rn(R, __uint_as_float(__float_as_uint(cs) ^ cflip));
     z2 = __fmul_rn(R, __uint_as_float(__float_as_uint(sn) ^ sflip));
 }

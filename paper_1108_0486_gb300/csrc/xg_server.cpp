@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "xg_batch.h"
+#include "xg_jump.h"
 #include "xg_runtime.h"
 
 namespace xg {
@@ -145,6 +146,14 @@ public:
             if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess)
                 return fail(XG_ECUDA, "server: stream creation failed");
             if (xg_status s = l.launcher->reserve(c_, cfg_.max_batch)) return fail(s, "server: batch launcher");
+            // room for requests cut into pieces, so the first ones do not allocate
+            if (xg_status s = l.launcher->reserve_jump(2048, 4096)) return fail(s, "server: jump buffers");
+        }
+        // the jump powers a cut request can need (pieces of 2^16..2^22 words,
+        // calls up to 2^32 words), built now rather than on the first request
+        for (int k = 0; k <= 32; ++k) {
+            xg_status st = XG_OK;
+            if (!jump_matrix(c_->device, (int)c_->param_set, k, lanes_[0].stream, &st)) return st;
         }
         // host-side fault injection for tests: the first N batch launches
         // report failure without reaching the GPU
