@@ -132,10 +132,13 @@ __global__ void __launch_bounds__(64) gf2_apply_partial_kernel(const uint64_t* _
 }
 
 // dst[i] ^= C src[i] for n (src, dst) pairs, dst zeroed beforehand.  Block
-// (x, y): pairs [8x, 8x+8), columns [y*cols, (y+1)*cols); 128 threads, thread
-// t owns 32-bit word t of every result and folds its partial XOR into dst
-// with one atomic XOR per pair.
-constexpr int kPairVecs = 8;
+// (x, y): pairs [16x, 16x+16), columns [y*cols, (y+1)*cols); 128 threads,
+// thread t owns 32-bit word t of every result.  Columns go four at a time:
+// each thread tabulates the 16 XOR combinations of its word of the four
+// columns (in shared memory, its own column of the table, so no barrier is
+// needed), and a state then costs one lookup and one XOR per four columns.
+// Partial results are folded into dst with one atomic XOR per pair.
+constexpr int kPairVecs = 16;
 __global__ void __launch_bounds__(128) gf2_apply_pairs_kernel(const uint32_t* __restrict__ C,
                                                               const uint32_t* __restrict__ rings,
                                                               const uint32_t* __restrict__ src,
@@ -143,6 +146,7 @@ __global__ void __launch_bounds__(128) gf2_apply_pairs_kernel(const uint32_t* __
                                                               uint32_t* __restrict__ out, int cols)
 {
     __shared__ uint32_t vbits[kPairVecs][kR];
+    __shared__ uint32_t tbl[16][kR];
     const int t = threadIdx.x;
     const uint32_t base = blockIdx.x * kPairVecs;
     const int nv = (int)umin((uint32_t)kPairVecs, n - base);
@@ -154,19 +158,23 @@ __global__ void __launch_bounds__(128) gf2_apply_pairs_kernel(const uint32_t* __
     for (int v = 0; v < kPairVecs; ++v) acc[v] = 0;
     const int w0 = blockIdx.y * (cols / 32), w1 = w0 + cols / 32;
     for (int w = w0; w < w1; ++w) {  // 32 columns per input word
-        // all 32 column words first (independent loads in flight together)
         const uint32_t* colw = C + (size_t)w * 32 * kR + t;
         uint32_t col[32];
 #pragma unroll
         for (int b = 0; b < 32; ++b) col[b] = __ldg(colw + (size_t)b * kR);
+        uint32_t bw[kPairVecs];
 #pragma unroll
-        for (int v = 0; v < kPairVecs; ++v) {
-            const uint32_t bw = vbits[v][w];
+        for (int v = 0; v < kPairVecs; ++v) bw[v] = vbits[v][w];
 #pragma unroll
-            for (int b = 0; b < 32; ++b) {
-                const uint32_t m = (uint32_t)((int32_t)(bw << (31 - b)) >> 31);
-                acc[v] ^= col[b] & m;
-            }
+        for (int g = 0; g < 8; ++g) {
+            const uint32_t c0 = col[4 * g], c1 = col[4 * g + 1], c2 = col[4 * g + 2], c3 = col[4 * g + 3];
+            const uint32_t c01 = c0 ^ c1, c23 = c2 ^ c3;
+            tbl[0][t] = 0u;        tbl[1][t] = c0;         tbl[2][t] = c1;         tbl[3][t] = c01;
+            tbl[4][t] = c2;        tbl[5][t] = c2 ^ c0;    tbl[6][t] = c2 ^ c1;    tbl[7][t] = c2 ^ c01;
+            tbl[8][t] = c3;        tbl[9][t] = c3 ^ c0;    tbl[10][t] = c3 ^ c1;   tbl[11][t] = c3 ^ c01;
+            tbl[12][t] = c23;      tbl[13][t] = c23 ^ c0;  tbl[14][t] = c23 ^ c1;  tbl[15][t] = c23 ^ c01;
+#pragma unroll
+            for (int v = 0; v < kPairVecs; ++v) acc[v] ^= tbl[(bw[v] >> (4 * g)) & 15u][t];
         }
     }
 #pragma unroll
