@@ -27,6 +27,7 @@ Parity status (each pin lives in ``tests/test_oracle_pins.py``):
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -60,56 +61,78 @@ class _Gen(ctypes.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle's C sources into a shared library (gcc, -O2)."""
+def build(force: bool = False, plant: int = 0) -> str:
+    """Compile the oracle's C sources into a shared library (gcc, -O2).
+    plant != 0 builds a variant with a deliberate mistake (tests only)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
-    if not force and os.path.exists(_LIB_PATH):
+    path = _LIB_PATH if plant == 0 else os.path.join(_LIB_DIR, f"liboracle_plant{plant}.so")
+    if not force and os.path.exists(path):
         newest = max(os.path.getmtime(s) for s in srcs)
-        if os.path.getmtime(_LIB_PATH) >= newest:
-            return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
-           "-o", tmp, *srcs, "-lm"]
+        if os.path.getmtime(path) >= newest:
+            return path
+    tmp = path + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", f"-DXGO_PLANT={int(plant)}", "-fPIC",
+           "-shared", "-o", tmp, *srcs, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def _declare(L):
+    u32, u64, p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+    G = ctypes.POINTER(_Gen)
+    L.xgo_sizeof.restype = ctypes.c_size_t
+    assert L.xgo_sizeof() == ctypes.sizeof(_Gen), "oracle struct layout mismatch"
+    L.xgo_omega.argtypes = [u32]; L.xgo_omega.restype = u32
+    L.xgo_init.argtypes = [G, u32, u32, u32, u32, u32, u32, u32, u32]
+    L.xgo_init.restype = ctypes.c_int
+    L.xgo_set_state.argtypes = [G, p, u32]
+    L.xgo_get_state.argtypes = [G, p, p]
+    L.xgo_step.argtypes = [G]; L.xgo_step.restype = u32
+    L.xgo_next.argtypes = [G]; L.xgo_next.restype = u32
+    L.xgo_combine.argtypes = [G, u32, u32]; L.xgo_combine.restype = u32
+    L.xgo_seed32.argtypes = [G, u32]; L.xgo_seed32.restype = ctypes.c_int
+    L.xgo_uniform.argtypes = [u32]; L.xgo_uniform.restype = ctypes.c_float
+    L.xgo_normal_pair.argtypes = [u32, u32, p, p]
+    L.xgo_normal_pairs.argtypes = [p, u64, p]
+    for f in ("xgo_fill_u32", "xgo_fill_raw", "xgo_fill_uniform", "xgo_fill_normal"):
+        getattr(L, f).argtypes = [G, u64, p]
+    L.xgo_sum_normal.argtypes = [G, u64]; L.xgo_sum_normal.restype = ctypes.c_double
+    L.xgo_streams.argtypes = [u32, u32, u32, u32, u32, u32, u32, p, u32, u64,
+                              ctypes.c_int, p]
+    L.xgo_streams.restype = ctypes.c_int
+    L.xgo_cycle_length.argtypes = [G, u64]; L.xgo_cycle_length.restype = u64
+    L.xgo_berlekamp_massey.argtypes = [p, ctypes.c_int, p]
+    L.xgo_berlekamp_massey.restype = ctypes.c_int
+    L.xgo_poly_irreducible.argtypes = [p, ctypes.c_int]
+    L.xgo_poly_irreducible.restype = ctypes.c_int
+    return L
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            u32, u64, p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
-            G = ctypes.POINTER(_Gen)
-            L.xgo_sizeof.restype = ctypes.c_size_t
-            assert L.xgo_sizeof() == ctypes.sizeof(_Gen), "oracle struct layout mismatch"
-            L.xgo_omega.argtypes = [u32]; L.xgo_omega.restype = u32
-            L.xgo_init.argtypes = [G, u32, u32, u32, u32, u32, u32, u32, u32]
-            L.xgo_init.restype = ctypes.c_int
-            L.xgo_set_state.argtypes = [G, p, u32]
-            L.xgo_get_state.argtypes = [G, p, p]
-            L.xgo_step.argtypes = [G]; L.xgo_step.restype = u32
-            L.xgo_next.argtypes = [G]; L.xgo_next.restype = u32
-            L.xgo_combine.argtypes = [G, u32, u32]; L.xgo_combine.restype = u32
-            L.xgo_seed32.argtypes = [G, u32]; L.xgo_seed32.restype = ctypes.c_int
-            L.xgo_uniform.argtypes = [u32]; L.xgo_uniform.restype = ctypes.c_float
-            L.xgo_normal_pair.argtypes = [u32, u32, p, p]
-            L.xgo_normal_pairs.argtypes = [p, u64, p]
-            for f in ("xgo_fill_u32", "xgo_fill_raw", "xgo_fill_uniform", "xgo_fill_normal"):
-                getattr(L, f).argtypes = [G, u64, p]
-            L.xgo_sum_normal.argtypes = [G, u64]; L.xgo_sum_normal.restype = ctypes.c_double
-            L.xgo_streams.argtypes = [u32, u32, u32, u32, u32, u32, u32, p, u32, u64,
-                                      ctypes.c_int, p]
-            L.xgo_streams.restype = ctypes.c_int
-            L.xgo_cycle_length.argtypes = [G, u64]; L.xgo_cycle_length.restype = u64
-            L.xgo_berlekamp_massey.argtypes = [p, ctypes.c_int, p]
-            L.xgo_berlekamp_massey.restype = ctypes.c_int
-            L.xgo_poly_irreducible.argtypes = [p, ctypes.c_int]
-            L.xgo_poly_irreducible.restype = ctypes.c_int
-            _lib = L
+            _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def planted(plant: int):
+    """Temporarily route every oracle call to a variant built with a
+    deliberate mistake (XGO_PLANT in xorgens_oracle.c); for the tests that
+    check that the pins catch such mistakes."""
+    global _lib
+    lib()
+    with _lock:
+        saved = _lib
+        _lib = _declare(ctypes.CDLL(build(plant=plant)))
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
 
 
 def _ptr(a: np.ndarray) -> int:

@@ -37,6 +37,16 @@
 #include <stdint.h>
 #include <string.h>
 
+/* XGO_PLANT selects a deliberate mistake, for the tests that check that the
+ * pins catch it (tests/test_oracle_planted.py builds such variants); the
+ * oracle proper is compiled with XGO_PLANT = 0.
+ *   1: the lag-s term is dropped        2: (I + R^b) shifts the wrong way
+ *   3: the lags' operator pairs swapped 4: the Weyl shift gamma is w/2 - 1
+ *   5: the Weyl word is used before it is advanced */
+#ifndef XGO_PLANT
+#define XGO_PLANT 0
+#endif
+
 #define XGO_RMAX 256
 
 typedef struct {
@@ -71,6 +81,9 @@ int xgo_init(xgo_gen* g, uint32_t w, uint32_t r, uint32_t s, uint32_t a,
     g->mask = (w == 32) ? 0xFFFFFFFFu : ((1u << w) - 1u);
     g->omega = xgo_omega(w) & g->mask;
     g->gamma = w / 2;
+#if XGO_PLANT == 4
+    g->gamma = w / 2 - 1;
+#endif
     return 0;
 }
 
@@ -98,10 +111,20 @@ uint32_t xgo_step(xgo_gen* g)
     const uint32_t m = g->mask;
     uint32_t t = g->x[g->i];                            /* x_{k-r} */
     uint32_t v = g->x[(g->i + g->r - g->s) % g->r];     /* x_{k-s} */
+#if XGO_PLANT == 3
+    { uint32_t tmp = t; t = v; v = tmp; }
+#endif
     t = (t ^ (t << g->a)) & m;                          /* t (I + L^a) */
+#if XGO_PLANT == 2
+    t = (t ^ (t << g->b)) & m;
+#else
     t = t ^ (t >> g->b);                                /*   (I + R^b) */
+#endif
     v = (v ^ (v << g->c)) & m;                          /* v (I + L^c) */
     v = v ^ (v >> g->d);                                /*   (I + R^d) */
+#if XGO_PLANT == 1
+    v = 0;
+#endif
     uint32_t xk = t ^ v;                                /* GF(2) sum  */
     g->x[g->i] = xk;                                    /* replaces x_{k-r} */
     g->i = (g->i + 1) % g->r;
@@ -120,8 +143,14 @@ uint32_t xgo_combine(const xgo_gen* g, uint32_t xk, uint32_t wk)
 /* Next output word of the generator. */
 uint32_t xgo_next(xgo_gen* g)
 {
+#if XGO_PLANT == 5
+    uint32_t w_before = g->weyl;
+    uint32_t xk = xgo_step(g);
+    return g->weyl_on ? xgo_combine(g, xk, w_before) : xk;
+#else
     uint32_t xk = xgo_step(g);
     return g->weyl_on ? xgo_combine(g, xk, g->weyl) : xk;
+#endif
 }
 
 /* Marsaglia's 64-bit xorshift with the published shift triple (13, 7, 17)

@@ -1,0 +1,41 @@
+"""The pins catch planted mistakes.
+
+Each case rebuilds the oracle with one deliberate mistake (XGO_PLANT in
+oracle/xorgens_oracle.c), routes the oracle to it, and checks that the pin
+aimed at that kind of mistake fails, and that the stored golden outputs no
+longer reproduce.  The oracle proper is untouched."""
+import pytest
+
+import oracle as O
+import test_oracle_pins as pins
+
+CASES = {
+    1: ("the lag-s term dropped", [lambda: pins.test_impulse_response_closed_form(0),
+                                    lambda: pins.test_lag_dependency(0),
+                                    lambda: pins.test_minimal_polynomial_irreducible_degree_4096(0)]),
+    2: ("(I + R^b) shifting the wrong way", [lambda: pins.test_impulse_response_closed_form(0),
+                                              lambda: pins.test_minimal_polynomial_irreducible_degree_4096(1)]),
+    3: ("the operator pairs of the two lags swapped",
+        [lambda: pins.test_impulse_response_closed_form(1),
+         lambda: pins.test_minimal_polynomial_irreducible_degree_4096(0)]),
+    4: ("the Weyl shift gamma off by one", [pins.test_weyl_combination_invariant]),
+    5: ("the Weyl word used before it is advanced", [pins.test_weyl_combination_invariant]),
+}
+
+
+@pytest.mark.parametrize("plant", sorted(CASES))
+def test_pins_catch_planted_mistake(plant):
+    what, checks = CASES[plant]
+    with O.planted(plant):
+        for check in checks:
+            with pytest.raises(AssertionError):
+                check()
+        with pytest.raises(AssertionError):
+            pins.test_golden_regression()
+
+
+def test_unplanted_oracle_passes_the_same_checks():
+    for _, checks in CASES.values():
+        for check in checks:
+            check()
+    pins.test_golden_regression()
