@@ -367,6 +367,17 @@ def extra_rows(st, stream, torch, peak):
     ms = _time(lambda: st.u32(n, out=buf.view(torch.int32)), stream, torch)
     rows["u32"] = {"rn_s": rn / (ms / 1e3), "ms": ms, "hbm_frac": rn * 4 / (ms / 1e3) / 1e9 / peak}
     del buf
+    # one stream, 2^20 words (seed 0x12345678): latency of a single long call
+    from paper_1108_0486_gb300 import Streams
+    one = Streams(1, seeds=[W.SINGLE_STREAM["seed"]], stream=stream)
+    nb = W.SINGLE_STREAM["n"]
+    ob = torch.empty(nb, dtype=torch.int32, device="cuda")
+    ms_cut = _time(lambda: one.u32(nb, out=ob.view(1, nb)), stream, torch)
+    one.set_batch_split(1)
+    ms_serial = _time(lambda: one.u32(nb, out=ob.view(1, nb)), stream, torch)
+    one.close()
+    rows["single_stream_2p20_u32"] = {"ms": ms_cut, "rn_s": nb / (ms_cut / 1e3),
+                                      "ms_one_warp_uncut": ms_serial}
     return rows
 
 
@@ -566,7 +577,11 @@ def profile_kernel(args):
     if args.kernel in ("normal", "normal_sum", "u32", "uniform"):
         st = Streams(STREAMS, seeds=W.seeds(STREAMS), stream=stream)
         kind = "normal" if args.kernel.startswith("normal") else args.kernel
-        if not args.no_autotune:
+        if args.launch:
+            tpg, wpl = (int(v) for v in args.launch.split(","))
+            st.set_launch(kind, tpg, wpl)
+            out["launch"] = {"tpg": tpg, "wpl": wpl, "block": "default of the configuration"}
+        elif not args.no_autotune:
             out["launch"] = st.autotune(kind, n)
         if args.kernel == "normal_sum":
             sums = torch.empty(STREAMS, dtype=torch.float32, device="cuda")
@@ -603,6 +618,8 @@ def main():
                     help="time one kernel's workload alone (profiling case; not a bench line)")
     ap.add_argument("--n-per", type=int, default=None,
                     help="override words per stream (profiling of a smaller case; not a bench line)")
+    ap.add_argument("--launch", default=None,
+                    help="profiling case: fixed lanes,words per lane (e.g. 8,4) instead of autotuning")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
     args = ap.parse_args()

@@ -111,7 +111,10 @@ xg_status xg_set_state(xg_ctx* ctx, uint32_t stream, const uint32_t* host_ring12
  * memory (the library generates into its own device buffer in chunks and
  * copies them to the host, overlapping both; returns when the data is there).
  * The fast path needs out and ld*4 bytes 16-byte aligned; other alignments
- * are accepted and use scalar stores. */
+ * are accepted and use scalar stores.  Calls on at most 64 streams with at
+ * least 2^18 outputs each go through the batch path, which cuts them into
+ * pieces generated at once (see xg_set_batch_split; 1 turns this off); the
+ * outputs are the same. */
 xg_status xg_generate_u32(xg_ctx* ctx, uint32_t first, uint32_t nstreams,
                           uint64_t n_per_stream, uint32_t* out, uint64_t ld);
 xg_status xg_generate_uniform(xg_ctx* ctx, uint32_t first, uint32_t nstreams,

@@ -118,6 +118,28 @@ static xg_status enqueue_gen(Ctx* c, int kind, uint32_t first, uint32_t nstreams
     return XG_OK;
 }
 
+constexpr uint32_t kCutMaxStreams = 64;
+constexpr uint64_t kCutMinWords = uint64_t(1) << 18;
+
+static xg_status generate_cut(Ctx* c, int kind, uint32_t first, uint32_t nstreams, uint64_t n, void* out,
+                              uint64_t ld)
+{
+    std::vector<xg::HostItem> items(nstreams);
+    for (uint32_t i = 0; i < nstreams; ++i)
+        items[i] = xg::HostItem{first + i, (uint32_t)kind, n, static_cast<char*>(out) + (uint64_t)i * ld * 4,
+                                nullptr};
+    xg::BatchLauncher*& L = c->batch[c->batch_next];
+    c->batch_next ^= 1;
+    if (!L) L = new (std::nothrow) xg::BatchLauncher();
+    if (!L) return fail(XG_ENOMEM, "host allocation failed");
+    xg_status st = L->launch(c, items.data(), nstreams, c->stream);
+    if (st != XG_OK) {
+        cudaError_t e = cudaGetLastError();
+        return fail(st, "cut generation failed (%s)", cudaGetErrorString(e));
+    }
+    return XG_OK;
+}
+
 static bool is_device_pointer(const void* p)
 {
     cudaPointerAttributes attr{};
@@ -193,7 +215,14 @@ static xg_status generate_common(xg_ctx* ctx, int kind, uint32_t first, uint32_t
     if (reinterpret_cast<uintptr_t>(out) & 3u) return fail(XG_EINVAL, "output must be 4-byte aligned");
     if (c->server) return fail(XG_EINVAL, "the request server owns this context; use xg_submit");
     std::lock_guard<std::mutex> lk(c->mu);
-    if (is_device_pointer(out)) return enqueue_gen(c, kind, first, nstreams, n, out, ld, nullptr, c->stream);
+    if (is_device_pointer(out)) {
+        // few streams, long calls: a single stream is one serial chain (one
+        // warp, ~1.5e9 words/s), so cut each call into pieces that run on
+        // many warps at once (jump-ahead; the output is the same)
+        if (nstreams <= kCutMaxStreams && n >= kCutMinWords && c->split_words != 1)
+            return generate_cut(c, kind, first, nstreams, n, out, ld);
+        return enqueue_gen(c, kind, first, nstreams, n, out, ld, nullptr, c->stream);
+    }
     return generate_to_host(c, kind, first, nstreams, n, out, ld);
 }
 
