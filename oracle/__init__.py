@@ -4,26 +4,33 @@ Plain, slow, serial CPU implementation of the xorgens generator of
 Nandapalan, Brent, Murray and Rendell (arXiv:1108.0486): the recurrence and
 circular buffer of Sec. 2, the Weyl generator and output combination of
 Sec. 1.5 Eq. (1), and this project's uniform / Box-Muller conversions (FP64).
-The arithmetic lives in ``xorgens_oracle.c`` (generator) and ``gf2.c``
-(Berlekamp-Massey and Rabin's irreducibility test, used only to pin the
-recurrence); this module compiles them with gcc and wraps them with ctypes.
+The arithmetic lives in ``xorgens_oracle.c`` (32-bit words),
+``xorgens64_oracle.c`` (64-bit words, FP64 uniforms) and ``gf2.c``
+(Berlekamp-Massey, Rabin's irreducibility test and powers of z modulo a
+polynomial, used only to pin the recurrence); this module compiles them with
+gcc and wraps them with ctypes.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s cpu_baseline /
 reference legs may import this package.  It shares no code with the GPU
 library and never imports it.
 
-Parity status (each pin lives in ``tests/test_oracle_pins.py``):
-  * recurrence, circular buffer   -- pinned (irreducible degree-4096 minimal
-    polynomial for both published parameter sets, impulse responses in closed
-    form, lag dependency, GF(2) linearity, tiny sets by brute-force period)
+Parity status (pins in ``tests/test_oracle_pins.py`` and
+``tests/test_oracle_w64_pins.py``):
+  * recurrence, circular buffer   -- pinned (primitive degree-4096 minimal
+    polynomial for both published parameter sets and for the 64-bit set,
+    impulse responses in closed form, lag dependency, GF(2) linearity, tiny
+    sets by brute-force period)
   * Weyl word and Eq. (1)         -- pinned (closed form of omega, invariant
-    out_k - x_k = h(w_0 + k omega))
-  * uniform conversion            -- pinned (exact closed form)
+    out_k - x_k = h(w_0 + k omega)), for w = 32 and w = 64
+  * uniform conversions           -- pinned (exact closed forms, FP32 and FP64)
   * Box-Muller in FP64            -- pinned (special points, against
     math.sin/cos on the reduced angle, moments)
+  * primitivity test              -- pinned (brute-force orders of z on all
+    degree-8 polynomials and all tiny w = 8 sets; the factor list of
+    2^4096 - 1 multiplied out and tested for primality)
   * seeding (project definition)  -- parity unpinned: the paper defers to the
     xorgens package, which is not available; only determinism and
-    distinctness are checked.
+    distinctness are checked (both word sizes).
 """
 from __future__ import annotations
 
@@ -36,7 +43,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ("xorgens_oracle.c", "gf2.c")
+_SOURCES = ("xorgens_oracle.c", "xorgens64_oracle.c", "gf2.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_LIB_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -58,6 +65,15 @@ class _Gen(ctypes.Structure):
         ("d", ctypes.c_uint32), ("weyl_on", ctypes.c_uint32), ("mask", ctypes.c_uint32),
         ("omega", ctypes.c_uint32), ("gamma", ctypes.c_uint32), ("i", ctypes.c_uint32),
         ("weyl", ctypes.c_uint32), ("k", ctypes.c_uint64), ("x", ctypes.c_uint32 * 256),
+    ]
+
+
+class _Gen64(ctypes.Structure):
+    _fields_ = [
+        ("r", ctypes.c_uint32), ("s", ctypes.c_uint32), ("a", ctypes.c_uint32),
+        ("b", ctypes.c_uint32), ("c", ctypes.c_uint32), ("d", ctypes.c_uint32),
+        ("weyl_on", ctypes.c_uint32), ("i", ctypes.c_uint32), ("omega", ctypes.c_uint64),
+        ("weyl", ctypes.c_uint64), ("k", ctypes.c_uint64), ("x", ctypes.c_uint64 * 256),
     ]
 
 
@@ -107,6 +123,26 @@ def _declare(L):
     L.xgo_berlekamp_massey.restype = ctypes.c_int
     L.xgo_poly_irreducible.argtypes = [p, ctypes.c_int]
     L.xgo_poly_irreducible.restype = ctypes.c_int
+    L.xgo_poly_zpow.argtypes = [p, ctypes.c_int, p, ctypes.c_int, p]
+    L.xgo_poly_zpow.restype = ctypes.c_int
+    L.xgo_poly_small_factor.argtypes = [p, ctypes.c_int, ctypes.c_int]
+    L.xgo_poly_small_factor.restype = ctypes.c_int
+    G64 = ctypes.POINTER(_Gen64)
+    L.xgo64_sizeof.restype = ctypes.c_size_t
+    assert L.xgo64_sizeof() == ctypes.sizeof(_Gen64), "oracle struct layout mismatch (w = 64)"
+    L.xgo64_omega.restype = u64
+    L.xgo64_init.argtypes = [G64, u32, u32, u32, u32, u32, u32, u32]
+    L.xgo64_init.restype = ctypes.c_int
+    L.xgo64_set_state.argtypes = [G64, p, u64]
+    L.xgo64_get_state.argtypes = [G64, p, p]
+    L.xgo64_step.argtypes = [G64]; L.xgo64_step.restype = u64
+    L.xgo64_next.argtypes = [G64]; L.xgo64_next.restype = u64
+    L.xgo64_seed.argtypes = [G64, u32]; L.xgo64_seed.restype = ctypes.c_int
+    L.xgo64_uniform.argtypes = [u64]; L.xgo64_uniform.restype = ctypes.c_double
+    for f in ("xgo64_fill_u64", "xgo64_fill_raw", "xgo64_fill_uniform"):
+        getattr(L, f).argtypes = [G64, u64, p]
+    L.xgo64_streams.argtypes = [u32, u32, u32, u32, u32, u32, u32, p, u32, u64, ctypes.c_int, p]
+    L.xgo64_streams.restype = ctypes.c_int
     return L
 
 
@@ -272,3 +308,179 @@ def is_irreducible(coeffs) -> bool:
     if rc < 0:
         raise ValueError("polynomial must be monic of degree >= 1")
     return bool(rc)
+
+
+def _exp_words(e: int) -> np.ndarray:
+    nw = max(1, (e.bit_length() + 63) // 64)
+    return np.array([(e >> (64 * i)) & 0xFFFFFFFFFFFFFFFF for i in range(nw)], dtype=np.uint64)
+
+
+def zpow(coeffs, e: int) -> np.ndarray:
+    """Coefficients (low to high, n of them) of z^e mod P, P = coeffs (degree n)."""
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.uint8) & 1)
+    n = c.size - 1
+    ew = _exp_words(int(e))
+    out = np.zeros(n, dtype=np.uint8)
+    if lib().xgo_poly_zpow(_ptr(c), n, _ptr(ew), ew.size, _ptr(out)):
+        raise ValueError("polynomial must be monic of degree >= 1")
+    return out
+
+
+def small_factor(coeffs, dmax: int) -> int:
+    """Smallest d <= dmax such that P has an irreducible factor of degree
+    dividing d (0: none)."""
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.uint8) & 1)
+    rc = lib().xgo_poly_small_factor(_ptr(c), c.size - 1, int(dmax))
+    if rc < 0:
+        raise ValueError("polynomial must be monic of degree >= 1")
+    return int(rc)
+
+
+def has_order(coeffs, order: int, prime_factors) -> bool:
+    """True iff z has multiplicative order exactly `order` modulo P, given the
+    distinct primes dividing `order` (Lidl and Niederreiter, Thm. 3.18 for
+    order = 2^n - 1: P is then primitive)."""
+    n = len(coeffs) - 1
+    one = np.zeros(n, dtype=np.uint8)
+    one[0] = 1
+    if not np.array_equal(zpow(coeffs, order), one):
+        return False
+    return all(not np.array_equal(zpow(coeffs, order // q), one) for q in prime_factors)
+
+
+# Known prime factors of the Fermat numbers F_k = 2^(2^k) + 1, k = 5 .. 11
+# (F_0 .. F_4 are prime; the largest factor of F_8 .. F_11 is the cofactor
+# left after dividing out these).  2^4096 - 1 = F_0 F_1 ... F_11.  The tests
+# check that the division is exact, that every factor passes Miller-Rabin and
+# has the form j 2^(k+2) + 1 that every prime factor of F_k has (Euler, Lucas).
+FERMAT_SMALL_FACTORS = {
+    5: (641, 6700417),
+    6: (274177, 67280421310721),
+    7: (59649589127497217, 5704689200685129054721),
+    8: (1238926361552897,),
+    9: (2424833, 7455602825647884208337395736200454918783366342657),
+    10: (45592577, 6487031809, 4659775785220018543264560743076778192897),
+    11: (319489, 974849, 167988556341760475137, 3560841906445833920513),
+}
+
+
+def fermat_factors(k: int):
+    """Prime factors of F_k (k <= 11), the last one as the exact cofactor."""
+    f = (1 << (1 << k)) + 1
+    out = []
+    for q in FERMAT_SMALL_FACTORS.get(k, ()):
+        assert f % q == 0
+        f //= q
+        out.append(q)
+    if f > 1:
+        out.append(f)
+    return out
+
+
+def mersenne_pow2_factors(n: int):
+    """Distinct primes of 2^n - 1 for n = 2^m, m <= 12."""
+    m = n.bit_length() - 1
+    assert n == 1 << m and m <= 12
+    return [q for k in range(m) for q in fermat_factors(k)]
+
+
+def is_primitive(coeffs) -> bool:
+    """P (degree n, a power of two <= 4096) is primitive: z has order 2^n - 1."""
+    n = len(coeffs) - 1
+    return has_order(coeffs, (1 << n) - 1, mersenne_pow2_factors(n))
+
+
+def minimal_polynomial_of_bits(bits) -> np.ndarray:
+    """Minimal polynomial (coefficients low to high) of a bit sequence: the
+    reciprocal of its Berlekamp-Massey connection polynomial."""
+    C = berlekamp_massey(bits)
+    return C[::-1].copy()
+
+
+# ---------------------------------------------------------------------------
+# 64-bit words (w = 64).  The paper's sets are for w = 32; this set, with the
+# same n = r w = 4096, was found by oracle/search_w64_params.py and its
+# primitivity is pinned in the tests.
+PARAM_SET_W64 = (64, 55, 42, 27, 25, 22)
+
+
+def omega64() -> int:
+    return int(lib().xgo64_omega())
+
+
+class Xorgens64:
+    """One serial xorgens generator with 64-bit words."""
+
+    def __init__(self, r, s, a, b, c, d, weyl=True):
+        self.g = _Gen64()
+        if lib().xgo64_init(ctypes.byref(self.g), r, s, a, b, c, d, int(bool(weyl))):
+            raise ValueError("invalid xorgens parameters")
+
+    @property
+    def r(self) -> int:
+        return self.g.r
+
+    def seed(self, seed: int) -> "Xorgens64":
+        lib().xgo64_seed(ctypes.byref(self.g), seed & 0xFFFFFFFF)
+        return self
+
+    def set_state(self, x_oldest_first, weyl: int) -> "Xorgens64":
+        x = np.ascontiguousarray(np.asarray(x_oldest_first, dtype=np.uint64))
+        assert x.size == self.g.r
+        lib().xgo64_set_state(ctypes.byref(self.g), _ptr(x), weyl & 0xFFFFFFFFFFFFFFFF)
+        return self
+
+    def get_state(self):
+        x = np.zeros(self.g.r, dtype=np.uint64)
+        w = np.zeros(1, dtype=np.uint64)
+        lib().xgo64_get_state(ctypes.byref(self.g), _ptr(x), _ptr(w))
+        return x, int(w[0])
+
+    def step(self) -> int:
+        return int(lib().xgo64_step(ctypes.byref(self.g)))
+
+    def next(self) -> int:
+        return int(lib().xgo64_next(ctypes.byref(self.g)))
+
+    @property
+    def weyl(self) -> int:
+        return int(self.g.weyl)
+
+    def u64(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint64)
+        lib().xgo64_fill_u64(ctypes.byref(self.g), n, _ptr(out))
+        return out
+
+    def raw(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint64)
+        lib().xgo64_fill_raw(ctypes.byref(self.g), n, _ptr(out))
+        return out
+
+    def uniform(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.float64)
+        lib().xgo64_fill_uniform(ctypes.byref(self.g), n, _ptr(out))
+        return out
+
+    def clone(self) -> "Xorgens64":
+        o = Xorgens64.__new__(Xorgens64)
+        o.g = _Gen64()
+        ctypes.pointer(o.g)[0] = self.g
+        return o
+
+
+def uniform64_of(words) -> np.ndarray:
+    f = lib().xgo64_uniform
+    return np.array([f(int(v)) for v in np.asarray(words, dtype=np.uint64).ravel()], dtype=np.float64)
+
+
+def streams64(seeds, n: int, kind: str = "u64", params=None, weyl=True) -> np.ndarray:
+    """n outputs from each freshly seeded 64-bit stream, shape (len(seeds), n)."""
+    params = PARAM_SET_W64 if params is None else params
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint32))
+    dt = {"u64": np.uint64, "uniform": np.float64}[kind]
+    out = np.empty((seeds.size, n), dtype=dt)
+    rc = lib().xgo64_streams(*params, int(bool(weyl)), _ptr(seeds), seeds.size, n,
+                             {"u64": 0, "uniform": 1}[kind], _ptr(out))
+    if rc:
+        raise ValueError("oracle stream generation failed")
+    return out

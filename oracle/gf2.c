@@ -168,3 +168,167 @@ int xgo_poly_irreducible(const uint8_t* coeffs, int n)
     bp_free(&p); bp_free(&x); bp_free(&g); bp_free(&a);
     return result;
 }
+
+/* ------------------------------------------------------------------------
+ * Powers of z modulo P, for the primitivity test.  A polynomial P of degree n
+ * is primitive iff it is irreducible and z has order exactly 2^n - 1 modulo P,
+ * i.e. z^((2^n-1)/q) != 1 for every prime q dividing 2^n - 1 (Lidl and
+ * Niederreiter, Finite Fields, Thm. 3.18).  For n a power of two, 2^n - 1 is
+ * the product of the Fermat numbers F_0 .. F_{log2 n - 1}, whose prime factors
+ * are known up to F_11 (n = 4096); the caller passes the exponents.
+ *
+ * Residues are n-bit vectors of nw = n/64 + 1 words.  Reduction of a product
+ * of degree < 2n - 1 takes its part above z^n eight bits at a time, highest
+ * first, using the table red[v] = v(z) z^n mod P (v < 256).
+ */
+typedef struct {
+    int n, nw;
+    uint64_t* red;   /* 256 * nw words */
+    uint64_t* prod;  /* 2 * nw + 2 words */
+} modp;
+
+static void mp_free(modp* m) { free(m->red); free(m->prod); m->red = m->prod = 0; }
+
+/* v := v z mod P (v has degree < n). */
+static void mp_mulz(const modp* m, const uint64_t* p, uint64_t* v)
+{
+    uint64_t carry = 0;
+    for (int k = 0; k < m->nw; ++k) {
+        uint64_t nc = v[k] >> 63;
+        v[k] = (v[k] << 1) | carry;
+        carry = nc;
+    }
+    if ((v[m->n >> 6] >> (m->n & 63)) & 1u)
+        for (int k = 0; k < m->nw; ++k) v[k] ^= p[k];
+}
+
+static int mp_init(modp* m, const uint64_t* p, int n)
+{
+    m->n = n;
+    m->nw = n / 64 + 1;
+    m->red = (uint64_t*)calloc((size_t)256 * m->nw, sizeof(uint64_t));
+    m->prod = (uint64_t*)calloc((size_t)2 * m->nw + 2, sizeof(uint64_t));
+    if (!m->red || !m->prod) { mp_free(m); return -1; }
+    /* basis[i] = z^(n+i) mod P for i < 8, built in red[1 << i] */
+    uint64_t* t = (uint64_t*)calloc((size_t)m->nw, sizeof(uint64_t));
+    if (!t) { mp_free(m); return -1; }
+    memcpy(t, p, (size_t)m->nw * sizeof(uint64_t));
+    t[n >> 6] ^= (uint64_t)1 << (n & 63);          /* z^n mod P = P - z^n */
+    for (int i = 0; i < 8; ++i) {
+        memcpy(m->red + (size_t)(1u << i) * m->nw, t, (size_t)m->nw * sizeof(uint64_t));
+        mp_mulz(m, p, t);
+    }
+    free(t);
+    for (int v = 1; v < 256; ++v) {
+        int low = v & -v;
+        if (v == low) continue;
+        uint64_t* d = m->red + (size_t)v * m->nw;
+        const uint64_t* x = m->red + (size_t)low * m->nw;
+        const uint64_t* y = m->red + (size_t)(v ^ low) * m->nw;
+        for (int k = 0; k < m->nw; ++k) d[k] = x[k] ^ y[k];
+    }
+    return 0;
+}
+
+static int mp_bit(const uint64_t* a, int i) { return (int)((a[i >> 6] >> (i & 63)) & 1u); }
+
+/* out := prod mod P, prod of degree < 2n - 1 (held in m->prod). */
+static void mp_reduce(const modp* m, uint64_t* out)
+{
+    const int n = m->n, nw = m->nw;
+    uint64_t* a = m->prod;
+    const int hbits = n - 1;                 /* bits n .. 2n-2 */
+    for (int j = (hbits + 7) / 8 - 1; j >= 0; --j) {
+        const int o = n + 8 * j;
+        unsigned v = 0;
+        for (int b = 7; b >= 0; --b) v = (v << 1) | (unsigned)mp_bit(a, o + b);
+        if (!v) continue;
+        const uint64_t* r = m->red + (size_t)v * nw;
+        const int ws = (8 * j) >> 6, bs = (8 * j) & 63;
+        for (int k = 0; k < nw; ++k) {
+            a[k + ws] ^= r[k] << bs;
+            if (bs) a[k + ws + 1] ^= r[k] >> (64 - bs);
+        }
+    }
+    memcpy(out, a, (size_t)nw * sizeof(uint64_t));
+    out[n >> 6] &= ((uint64_t)1 << (n & 63)) - 1;
+    for (int k = (n >> 6) + 1; k < nw; ++k) out[k] = 0;
+}
+
+/* v := v^2 mod P (squaring over GF(2) spreads the bits). */
+static void mp_square(const modp* m, uint64_t* v)
+{
+    uint64_t* a = m->prod;
+    memset(a, 0, (size_t)(2 * m->nw + 2) * sizeof(uint64_t));
+    for (int k = 0; k < m->nw; ++k) {
+        uint64_t x = v[k];
+        for (int h = 0; h < 2; ++h) {
+            uint64_t s = 0, y = (x >> (32 * h)) & 0xFFFFFFFFu;
+            for (int b = 0; b < 32; ++b) s |= ((y >> b) & 1u) << (2 * b);
+            a[2 * k + h] = s;
+        }
+    }
+    mp_reduce(m, v);
+}
+
+static int load_poly(const uint8_t* coeffs, int n, uint64_t** p)
+{
+    *p = (uint64_t*)calloc((size_t)(n / 64 + 1), sizeof(uint64_t));
+    if (!*p) return -1;
+    for (int i = 0; i <= n; ++i)
+        if (coeffs[i] & 1) (*p)[i >> 6] |= (uint64_t)1 << (i & 63);
+    return 0;
+}
+
+/* coefficients of z^e mod P into out[0..n); e is ne little-endian words.
+ * Left-to-right binary powering: square, then multiply by z where the
+ * exponent bit is set.  Returns 0, or -1 on a bad argument. */
+int xgo_poly_zpow(const uint8_t* coeffs, int n, const uint64_t* e, int ne, uint8_t* out)
+{
+    if (n < 1 || !(coeffs[n] & 1)) return -1;
+    uint64_t* p;
+    modp m;
+    if (load_poly(coeffs, n, &p)) return -1;
+    if (mp_init(&m, p, n)) { free(p); return -1; }
+    uint64_t* v = (uint64_t*)calloc((size_t)m.nw, sizeof(uint64_t));
+    if (!v) { mp_free(&m); free(p); return -1; }
+    v[0] = 1;
+    int top = ne * 64 - 1;
+    while (top >= 0 && !mp_bit(e, top)) --top;
+    for (int i = top; i >= 0; --i) {
+        mp_square(&m, v);
+        if (mp_bit(e, i)) mp_mulz(&m, p, v);
+    }
+    for (int i = 0; i < n; ++i) out[i] = (uint8_t)mp_bit(v, i);
+    free(v); mp_free(&m); free(p);
+    return 0;
+}
+
+/* Smallest d in [1, dmax] with gcd(z^(2^d) - z, P) != 1 (P then has an
+ * irreducible factor of degree dividing d), or 0 if there is none.  A quick
+ * screen before Rabin's test.  Returns -1 on a bad argument. */
+int xgo_poly_small_factor(const uint8_t* coeffs, int n, int dmax)
+{
+    if (n < 1 || !(coeffs[n] & 1)) return -1;
+    uint64_t* p;
+    modp m;
+    if (load_poly(coeffs, n, &p)) return -1;
+    if (mp_init(&m, p, n)) { free(p); return -1; }
+    bpoly a, g;
+    uint64_t* v = (uint64_t*)calloc((size_t)m.nw, sizeof(uint64_t));
+    if (!v || bp_alloc(&a, 2 * n + 2) || bp_alloc(&g, 2 * n + 2)) { mp_free(&m); free(p); return -1; }
+    v[0] = 1;
+    mp_mulz(&m, p, v);   /* z mod P */
+    int found = 0;
+    for (int d = 1; d <= dmax && !found; ++d) {
+        mp_square(&m, v);
+        memset(a.w, 0, (size_t)a.nw * sizeof(uint64_t));
+        memset(g.w, 0, (size_t)g.nw * sizeof(uint64_t));
+        memcpy(a.w, p, (size_t)m.nw * sizeof(uint64_t));
+        memcpy(g.w, v, (size_t)m.nw * sizeof(uint64_t));
+        bp_flip(&g, 1);
+        if (bp_gcd_deg(&a, &g) != 0) found = d;
+    }
+    free(v); bp_free(&a); bp_free(&g); mp_free(&m); free(p);
+    return found;
+}

@@ -39,3 +39,23 @@ def test_unplanted_oracle_passes_the_same_checks():
         for check in checks:
             check()
     pins.test_golden_regression()
+
+
+CASES_W64 = {
+    1: ["test_w64_impulse_response_closed_form", "test_w64_lag_dependency",
+        "test_w64_minimal_polynomial_primitive_degree_4096"],
+    2: ["test_w64_impulse_response_closed_form", "test_w64_minimal_polynomial_primitive_degree_4096"],
+    3: ["test_w64_impulse_response_closed_form", "test_w64_minimal_polynomial_primitive_degree_4096"],
+    4: ["test_w64_weyl_combination_invariant"],
+    5: ["test_w64_weyl_combination_invariant"],
+}
+
+
+@pytest.mark.parametrize("plant", sorted(CASES_W64))
+def test_w64_pins_catch_planted_mistake(plant):
+    """The same five mistakes planted in the 64-bit oracle."""
+    import test_oracle_w64_pins as p64
+    with O.planted(plant):
+        for name in CASES_W64[plant]:
+            with pytest.raises(AssertionError):
+                getattr(p64, name)()
