@@ -378,6 +378,22 @@ def extra_rows(st, stream, torch, peak):
     one.close()
     rows["single_stream_2p20_u32"] = {"ms": ms_cut, "rn_s": nb / (ms_cut / 1e3),
                                       "ms_one_warp_uncut": ms_serial}
+    # 64-bit words: 16384 streams x 2^16 FP64 uniforms (8 GiB) and raw u64
+    from paper_1108_0486_gb300 import Streams64
+    s64 = Streams64(STREAMS, seeds=W.seeds(STREAMS), stream=stream)
+    n64 = N_PER
+    b64 = torch.empty((STREAMS, n64), dtype=torch.float64, device="cuda")
+    tuned64 = s64.autotune("uniform", n64)
+    s64.autotune("u64", n64)
+    ms_f = _time(lambda: s64.uniform(n64, out=b64), stream, torch)
+    ms_u = _time(lambda: s64.u64(n64, out=b64.view(torch.int64)), stream, torch)
+    rn64 = STREAMS * n64
+    rows["w64_uniform_f64"] = {"rn_s": rn64 / (ms_f / 1e3), "ms": ms_f,
+                               "hbm_frac": rn64 * 8 / (ms_f / 1e3) / 1e9 / peak, "launch": tuned64}
+    rows["w64_u64"] = {"rn_s": rn64 / (ms_u / 1e3), "ms": ms_u,
+                       "hbm_frac": rn64 * 8 / (ms_u / 1e3) / 1e9 / peak}
+    s64.close()
+    del b64
     return rows
 
 
@@ -591,6 +607,17 @@ def profile_kernel(args):
                               device="cuda")
             fn = lambda: st.generate(kind, n, out=buf)
         out["ms"] = _time(fn, stream, torch, reps=args.steps, warm=args.warmup)
+    elif args.kernel == "w64_uniform":
+        from paper_1108_0486_gb300 import Streams64
+        st = Streams64(STREAMS, seeds=W.seeds(STREAMS), stream=stream)
+        if args.launch:
+            tpg, wpl = (int(v) for v in args.launch.split(","))
+            st.set_launch("uniform", tpg, wpl)
+            out["launch"] = {"tpg": tpg, "wpl": wpl, "block": "default of the configuration"}
+        elif not args.no_autotune:
+            out["launch"] = st.autotune("uniform", n)
+        buf = torch.empty((STREAMS, n), dtype=torch.float64, device="cuda")
+        out["ms"] = _time(lambda: st.uniform(n, out=buf), stream, torch, reps=args.steps, warm=args.warmup)
     elif args.kernel == "batch":
         items = [it for it in W.batched_uneven() if it.count <= n] if args.n_per else W.batched_uneven()
         st = Streams(4096, seeds=W.seeds(4096), stream=stream)
@@ -614,7 +641,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="arrival window of the serving row (10 s for the full 200K requests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["u32", "uniform", "normal", "normal_sum", "batch"],
+    ap.add_argument("--kernel", default=None, choices=["u32", "uniform", "normal", "normal_sum", "batch", "w64_uniform"],
                     help="time one kernel's workload alone (profiling case; not a bench line)")
     ap.add_argument("--n-per", type=int, default=None,
                     help="override words per stream (profiling of a smaller case; not a bench line)")

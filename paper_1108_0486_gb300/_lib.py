@@ -92,6 +92,18 @@ SIGNATURES = {
     "xg_autotune": [vp, i32, u32, u64, P_u32, P_u32, P_u32, ctypes.POINTER(ctypes.c_float)],
     "xg_last_error": [],
     "xg_version": [],
+    # 64-bit words (include/xorgens_w64.h)
+    "xg_w64_params": [P_u32, P_u64],
+    "xg_w64_create": [P_vp, u32, u32, vp],
+    "xg_w64_destroy": [vp],
+    "xg_w64_set_stream": [vp, vp],
+    "xg_w64_seed": [vp, u32, u32, vp],
+    "xg_w64_get_state": [vp, u32, vp, P_u64],
+    "xg_w64_set_state": [vp, u32, vp, u64],
+    "xg_w64_generate_u64": [vp, u32, u32, u64, vp, u64],
+    "xg_w64_generate_uniform_f64": [vp, u32, u32, u64, vp, u64],
+    "xg_w64_set_launch": [vp, i32, u32, u32, u32],
+    "xg_w64_autotune": [vp, i32, u32, u64, P_u32, P_u32, P_u32, ctypes.POINTER(ctypes.c_float)],
 }
 _RESTYPES = {"xg_last_error": ctypes.c_char_p, "xg_version": ctypes.c_char_p}
 
@@ -296,3 +308,62 @@ def xg_autotune(ctx, out_type, nstreams, n_per_stream):
 
 def xg_version() -> str:
     return lib().xg_version().decode()
+
+
+# ---- 64-bit words --------------------------------------------------------
+XG_W64_U64, XG_W64_UNIFORM_F64 = 0, 1
+
+
+def xg_w64_params():
+    v = (ctypes.c_uint32 * 6)()
+    om = ctypes.c_uint64()
+    call("xg_w64_params", v, ctypes.byref(om))
+    return tuple(v), om.value
+
+
+def xg_w64_create(n_streams: int, weyl_on: bool = True, cuda_stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    call("xg_w64_create", ctypes.byref(h), n_streams, int(bool(weyl_on)), ctypes.c_void_p(cuda_stream))
+    return h.value
+
+
+def xg_w64_destroy(ctx: int) -> None:
+    call("xg_w64_destroy", ctypes.c_void_p(ctx))
+
+
+def xg_w64_set_stream(ctx: int, cuda_stream: int) -> None:
+    call("xg_w64_set_stream", ctypes.c_void_p(ctx), ctypes.c_void_p(cuda_stream))
+
+
+def xg_w64_seed(ctx: int, first: int, count: int, host_seeds_ptr: int) -> None:
+    call("xg_w64_seed", ctypes.c_void_p(ctx), first, count, ctypes.c_void_p(host_seeds_ptr))
+
+
+def xg_w64_get_state(ctx: int, stream: int, host_ring_ptr: int) -> int:
+    w = ctypes.c_uint64()
+    call("xg_w64_get_state", ctypes.c_void_p(ctx), stream, ctypes.c_void_p(host_ring_ptr), ctypes.byref(w))
+    return w.value
+
+
+def xg_w64_set_state(ctx: int, stream: int, host_ring_ptr: int, weyl: int) -> None:
+    call("xg_w64_set_state", ctypes.c_void_p(ctx), stream, ctypes.c_void_p(host_ring_ptr), weyl)
+
+
+def xg_w64_generate_u64(ctx, first, nstreams, n_per_stream, out_ptr, ld) -> None:
+    call("xg_w64_generate_u64", ctypes.c_void_p(ctx), first, nstreams, n_per_stream, ctypes.c_void_p(out_ptr), ld)
+
+
+def xg_w64_generate_uniform_f64(ctx, first, nstreams, n_per_stream, out_ptr, ld) -> None:
+    call("xg_w64_generate_uniform_f64", ctypes.c_void_p(ctx), first, nstreams, n_per_stream,
+         ctypes.c_void_p(out_ptr), ld)
+
+
+def xg_w64_set_launch(ctx, out_type, tpg, wpl, block=0) -> None:
+    call("xg_w64_set_launch", ctypes.c_void_p(ctx), out_type, tpg, wpl, block)
+
+
+def xg_w64_autotune(ctx, out_type, nstreams, n_per_stream):
+    t, w, b, ms = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_float()
+    call("xg_w64_autotune", ctypes.c_void_p(ctx), out_type, nstreams, n_per_stream, ctypes.byref(t),
+         ctypes.byref(w), ctypes.byref(b), ctypes.byref(ms))
+    return {"tpg": t.value, "wpl": w.value, "block": b.value, "ms": ms.value}

@@ -250,3 +250,83 @@ def device_view(ptr: int, count: int, dtype=torch.float32) -> torch.Tensor:
 def as_u32(t: torch.Tensor) -> np.ndarray:
     """Copy an int32 bit-pattern tensor to host as numpy uint32."""
     return t.detach().cpu().numpy().view(np.uint32)
+
+
+TYPES_W64 = {"u64": L.XG_W64_U64, "uniform": L.XG_W64_UNIFORM_F64}
+LAUNCHES_W64 = [(4, 8), (8, 4), (16, 2), (32, 1)]
+
+
+class Streams64:
+    """A context of n independent 64-bit-word xorgens streams on the GPU
+    ((r,s,a,b,c,d) = (64,55,42,27,25,22)), with raw 64-bit outputs and FP64
+    uniforms.  Outputs: u64 as int64 bit patterns, uniforms as float64."""
+
+    def __init__(self, n: int, weyl: bool = True, stream=None, seeds=None):
+        self.n = int(n)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = L.xg_w64_create(self.n, weyl, _stream_handle(self.stream))
+        if seeds is not None:
+            self.seed(seeds)
+
+    @staticmethod
+    def params():
+        return L.xg_w64_params()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            L.xg_w64_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def seed(self, seeds, first: int = 0):
+        s = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint32).ravel())
+        L.xg_w64_seed(self.ctx, first, s.size, s.ctypes.data)
+        return self
+
+    def get_state(self, stream: int):
+        ring = np.zeros(64, dtype=np.uint64)
+        w = L.xg_w64_get_state(self.ctx, stream, ring.ctypes.data)
+        return ring, w
+
+    def set_state(self, stream: int, ring, weyl: int):
+        r = np.ascontiguousarray(np.asarray(ring, dtype=np.uint64))
+        assert r.size == 64
+        L.xg_w64_set_state(self.ctx, stream, r.ctypes.data, weyl)
+
+    def set_launch(self, kind: str, tpg: int = 0, wpl: int = 0, block: int = 0):
+        L.xg_w64_set_launch(self.ctx, TYPES_W64[kind], tpg, wpl, block)
+
+    def autotune(self, kind: str, n_per_stream: int, nstreams: int = 0) -> dict:
+        return L.xg_w64_autotune(self.ctx, TYPES_W64[kind], nstreams, n_per_stream)
+
+    def _gen(self, fn, dtype, n, first, count, out, ld):
+        count = self.n - first if count is None else count
+        if out is None:
+            ld = n if ld is None else ld
+            out = torch.empty((count, ld), dtype=dtype, device="cuda")
+        else:
+            ld = out.stride(0) if (ld is None and out.dim() == 2) else (ld if ld is not None else n)
+        fn(self.ctx, first, count, n, out.data_ptr(), ld)
+        return out
+
+    def u64(self, n: int, first: int = 0, count=None, out=None, ld=None):
+        """n words per stream as int64 bit patterns, shape (count, ld)."""
+        return self._gen(L.xg_w64_generate_u64, torch.int64, n, first, count, out, ld)
+
+    def uniform(self, n: int, first: int = 0, count=None, out=None, ld=None):
+        """n FP64 uniforms in [0, 1) per stream."""
+        return self._gen(L.xg_w64_generate_uniform_f64, torch.float64, n, first, count, out, ld)
+
+    def generate(self, kind: str, n: int, **kw):
+        return {"u64": self.u64, "uniform": self.uniform}[kind](n, **kw)

@@ -1,0 +1,360 @@
+// Host runtime of the 64-bit-word generators: contexts with device-resident
+// state, argument checking, launch choice, host-output staging, autotuning,
+// and the extern "C" entry points of include/xorgens_w64.h.
+#include "xorgens_w64.h"
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "xg_runtime.h"
+#include "xg_w64.h"
+
+using xg::cuda_fail;
+using xg::fail;
+
+struct xg_w64_ctx {
+    int device = 0;
+    int sm_count = 148;
+    uint32_t n = 0;
+    uint32_t weyl_on = 1;
+    cudaStream_t stream = nullptr;
+    void* state_mem = nullptr;
+    size_t state_bytes = 0;
+    xg64::State st{};
+    int cfg[2] = {-1, -1};
+    int blk[2] = {0, 0};
+    void* staging = nullptr;
+    size_t staging_bytes = 0;
+    std::mutex mu;
+};
+
+namespace {
+
+#define XG_CUDA(call, what)                                \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool is_device_pointer(const void* p)
+{
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+int pick_cfg(const xg_w64_ctx* c, int kind, uint32_t nstreams)
+{
+    if (c->cfg[kind] >= 0) return c->cfg[kind];
+    // many streams: few lanes per stream (fewer shuffles, 16-byte stores)
+    const uint64_t lanes_wanted = (uint64_t)c->sm_count * 32 * 24;
+    if ((uint64_t)nstreams * 8 >= lanes_wanted / 2) return xg64::cfg_index(8, 4);
+    if ((uint64_t)nstreams * 16 >= lanes_wanted / 2) return xg64::cfg_index(16, 2);
+    return xg64::cfg_index(32, 1);
+}
+
+xg_status enqueue(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstreams, uint64_t n, void* d_out,
+                  uint64_t ld, int force_cfg = -1, int force_block = 0)
+{
+    xg64::GenArgs a{};
+    a.st = c->st;
+    a.first = first;
+    a.nstreams = nstreams;
+    a.n = n;
+    a.out = d_out;
+    a.ld = ld;
+    a.omega = c->weyl_on ? xg64::kOmega : 0;
+    const int cfg = force_cfg >= 0 ? force_cfg : pick_cfg(c, kind, nstreams);
+    int block = force_block;
+    if (block <= 0) block = (c->cfg[kind] == cfg && c->blk[kind] > 0) ? c->blk[kind] : xg64::kCfgs[cfg].block;
+    const bool vec = ((reinterpret_cast<uintptr_t>(d_out) & 15u) == 0) && (nstreams == 1 || ld % 2 == 0);
+    cudaError_t e = xg64::launch_gen(cfg, kind, vec, block, a, c->stream);
+    return e == cudaSuccess ? XG_OK : cuda_fail(e, "64-bit generate kernel launch");
+}
+
+// Host output: generate into one device buffer piece by piece and copy each
+// piece out (synchronously); pieces split the stream range and, for long
+// requests, each stream's length.
+xg_status to_host(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstreams, uint64_t n, void* h_out,
+                  uint64_t ld)
+{
+    const size_t kPieceBytes = size_t(128) << 20;
+    if (c->staging_bytes < kPieceBytes) {
+        if (c->staging) cudaFree(c->staging);
+        c->staging = nullptr;
+        c->staging_bytes = 0;
+        XG_CUDA(cudaMalloc(&c->staging, kPieceBytes), "cudaMalloc(staging)");
+        c->staging_bytes = kPieceBytes;
+    }
+    const uint64_t words = kPieceBytes / 8;
+    const uint64_t ncols = std::max<uint64_t>(1, std::min<uint64_t>(n, words));
+    const uint64_t ld_stage = align_up(ncols, 2);
+    const uint32_t rows_per = (uint32_t)std::max<uint64_t>(1, words / ld_stage);
+    for (uint32_t r0 = 0; r0 < nstreams; r0 += rows_per) {
+        const uint32_t rows = std::min<uint32_t>(rows_per, nstreams - r0);
+        for (uint64_t c0 = 0; c0 < n; c0 += ncols) {
+            const uint64_t cols = std::min<uint64_t>(ncols, n - c0);
+            xg_status st = enqueue(c, kind, first + r0, rows, cols, c->staging, ld_stage);
+            if (st != XG_OK) return st;
+            char* dst = static_cast<char*>(h_out) + ((uint64_t)r0 * ld + c0) * 8;
+            XG_CUDA(cudaMemcpy2DAsync(dst, ld * 8, c->staging, ld_stage * 8, cols * 8, rows,
+                                      cudaMemcpyDeviceToHost, c->stream),
+                    "cudaMemcpy2DAsync(device to host)");
+        }
+    }
+    XG_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return XG_OK;
+}
+
+xg_status generate(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstreams, uint64_t n, void* out,
+                   uint64_t ld)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if ((uint64_t)first + nstreams > c->n)
+        return fail(XG_EINVAL, "streams [%u, %u) out of range (context has %u)", first, first + nstreams, c->n);
+    if (nstreams == 0 || n == 0) return XG_OK;
+    if (!out) return fail(XG_EINVAL, "null output pointer");
+    if (nstreams > 1 && ld < n)
+        return fail(XG_EINVAL, "ld (%llu) < n_per_stream (%llu)", (unsigned long long)ld, (unsigned long long)n);
+    if (nstreams == 1 && ld < n) ld = n;
+    if (ld > (UINT64_MAX / 16) / nstreams) return fail(XG_EINVAL, "output extent overflows");
+    if (reinterpret_cast<uintptr_t>(out) & 7u) return fail(XG_EINVAL, "output must be 8-byte aligned");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (is_device_pointer(out)) return enqueue(c, kind, first, nstreams, n, out, ld);
+    return to_host(c, kind, first, nstreams, n, out, ld);
+}
+
+}  // namespace
+
+extern "C" {
+
+xg_status xg_w64_params(uint32_t* rsabcd, uint64_t* omega)
+{
+    if (!rsabcd || !omega) return fail(XG_EINVAL, "null output");
+    const uint32_t v[6] = {xg64::kR, xg64::kS, xg64::kA, xg64::kB, xg64::kC, xg64::kD};
+    std::memcpy(rsabcd, v, sizeof v);
+    *omega = xg64::kOmega;
+    return XG_OK;
+}
+
+xg_status xg_w64_create(xg_w64_ctx** out, uint32_t n_streams, uint32_t weyl_on, void* cuda_stream)
+{
+    if (!out) return fail(XG_EINVAL, "null output handle");
+    *out = nullptr;
+    if (n_streams == 0) return fail(XG_EINVAL, "n_streams must be positive");
+    xg_w64_ctx* c = new (std::nothrow) xg_w64_ctx();
+    if (!c) return fail(XG_ENOMEM, "host allocation failed");
+    c->n = n_streams;
+    c->weyl_on = weyl_on ? 1u : 0u;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    const size_t off_weyl = align_up((size_t)n_streams * xg64::kWin * 8, 256);
+    const size_t off_pend = align_up(off_weyl + (size_t)n_streams * 8, 256);
+    const size_t off_pos = align_up(off_pend + (size_t)n_streams * 4, 256);
+    const size_t total = off_pos + (size_t)n_streams * 8;
+    if (e == cudaSuccess) e = cudaMalloc(&c->state_mem, total);
+    if (e != cudaSuccess) {
+        xg_status st = e == cudaErrorMemoryAllocation ? fail(XG_ENOMEM, "cudaMalloc(state, %zu bytes) failed", total)
+                                                      : cuda_fail(e, "create");
+        cudaGetLastError();
+        delete c;
+        return st;
+    }
+    c->state_bytes = total;
+    char* base = static_cast<char*>(c->state_mem);
+    c->st.win = reinterpret_cast<uint64_t*>(base);
+    c->st.weyl = reinterpret_cast<uint64_t*>(base + off_weyl);
+    c->st.pend = reinterpret_cast<uint32_t*>(base + off_pend);
+    c->st.pos = reinterpret_cast<uint64_t*>(base + off_pos);
+    e = cudaMemsetAsync(c->state_mem, 0, total, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        xg_status st = cuda_fail(e, "create");
+        xg_w64_destroy(c);
+        return st;
+    }
+    *out = c;
+    return XG_OK;
+}
+
+xg_status xg_w64_destroy(xg_w64_ctx* c)
+{
+    if (!c) return XG_OK;
+    if (c->state_mem) cudaStreamSynchronize(c->stream);
+    if (c->staging) cudaFree(c->staging);
+    if (c->state_mem) cudaFree(c->state_mem);
+    delete c;
+    return XG_OK;
+}
+
+xg_status xg_w64_set_stream(xg_w64_ctx* c, void* cuda_stream)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return XG_OK;
+}
+
+xg_status xg_w64_seed(xg_w64_ctx* c, uint32_t first, uint32_t count, const uint32_t* host_seeds)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if ((uint64_t)first + count > c->n) return fail(XG_EINVAL, "seed range out of bounds");
+    if (count == 0) return XG_OK;
+    if (!host_seeds) return fail(XG_EINVAL, "null seeds");
+    std::lock_guard<std::mutex> lk(c->mu);
+    uint32_t* d = nullptr;
+    XG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), (size_t)count * 4, c->stream), "cudaMallocAsync(seeds)");
+    cudaError_t e = cudaMemcpyAsync(d, host_seeds, (size_t)count * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = xg64::launch_seed(c->st, d, first, count, c->stream);
+    cudaError_t e2 = cudaFreeAsync(d, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "seed");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(seeds)");
+    if (!c->weyl_on)
+        XG_CUDA(cudaMemsetAsync(c->st.weyl + first, 0, (size_t)count * 8, c->stream), "cudaMemsetAsync");
+    return XG_OK;
+}
+
+xg_status xg_w64_get_state(xg_w64_ctx* c, uint32_t stream, uint64_t* ring, uint64_t* weyl)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if (stream >= c->n) return fail(XG_EINVAL, "stream %u out of range", stream);
+    if (!ring || !weyl) return fail(XG_EINVAL, "null output");
+    std::lock_guard<std::mutex> lk(c->mu);
+    uint64_t win[xg64::kWin], w = 0;
+    uint32_t pend = 0;
+    XG_CUDA(cudaMemcpyAsync(win, c->st.win + (size_t)stream * xg64::kWin, sizeof win, cudaMemcpyDeviceToHost,
+                            c->stream), "get_state");
+    XG_CUDA(cudaMemcpyAsync(&pend, c->st.pend + stream, 4, cudaMemcpyDeviceToHost, c->stream), "get_state");
+    XG_CUDA(cudaMemcpyAsync(&w, c->st.weyl + stream, 8, cudaMemcpyDeviceToHost, c->stream), "get_state");
+    XG_CUDA(cudaStreamSynchronize(c->stream), "get_state");
+    if (pend >= (uint32_t)xg64::kRingBase) return fail(XG_EDEVICE, "corrupt stream state (pend %u)", pend);
+    std::memcpy(ring, win + xg64::kRingBase - pend, xg64::kR * 8);
+    *weyl = w;
+    return XG_OK;
+}
+
+xg_status xg_w64_set_state(xg_w64_ctx* c, uint32_t stream, const uint64_t* ring, uint64_t weyl)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if (stream >= c->n) return fail(XG_EINVAL, "stream %u out of range", stream);
+    if (!ring) return fail(XG_EINVAL, "null ring");
+    std::lock_guard<std::mutex> lk(c->mu);
+    uint64_t win[xg64::kWin] = {0};
+    std::memcpy(win + xg64::kRingBase, ring, xg64::kR * 8);
+    const uint32_t pend = 0;
+    const uint64_t w = c->weyl_on ? weyl : 0;
+    XG_CUDA(cudaMemcpyAsync(c->st.win + (size_t)stream * xg64::kWin, win, sizeof win, cudaMemcpyHostToDevice,
+                            c->stream), "set_state");
+    XG_CUDA(cudaMemcpyAsync(c->st.pend + stream, &pend, 4, cudaMemcpyHostToDevice, c->stream), "set_state");
+    XG_CUDA(cudaMemcpyAsync(c->st.weyl + stream, &w, 8, cudaMemcpyHostToDevice, c->stream), "set_state");
+    XG_CUDA(cudaStreamSynchronize(c->stream), "set_state");
+    return XG_OK;
+}
+
+xg_status xg_w64_generate_u64(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t n, uint64_t* out,
+                              uint64_t ld)
+{
+    return generate(c, xg64::kU64, first, nstreams, n, out, ld);
+}
+
+xg_status xg_w64_generate_uniform_f64(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t n, double* out,
+                                      uint64_t ld)
+{
+    return generate(c, xg64::kUniformF64, first, nstreams, n, out, ld);
+}
+
+xg_status xg_w64_set_launch(xg_w64_ctx* c, xg_w64_type type, uint32_t tpg, uint32_t wpl, uint32_t block)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if ((unsigned)type > XG_W64_UNIFORM_F64) return fail(XG_EINVAL, "unknown output type");
+    if (block > 1024 || (block & 31u)) return fail(XG_EINVAL, "block must be a multiple of 32, at most 1024");
+    if (tpg == 0 && wpl == 0) {
+        c->cfg[type] = -1;
+        c->blk[type] = 0;
+        return XG_OK;
+    }
+    const int ci = xg64::cfg_index((int)tpg, (int)wpl);
+    if (ci < 0) return fail(XG_EINVAL, "unsupported launch (tpg %u, wpl %u)", tpg, wpl);
+    c->cfg[type] = ci;
+    c->blk[type] = (int)block;
+    return XG_OK;
+}
+
+xg_status xg_w64_autotune(xg_w64_ctx* c, xg_w64_type type, uint32_t nstreams, uint64_t n_per_stream,
+                          uint32_t* tpg, uint32_t* wpl, uint32_t* block, float* best_ms)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if ((unsigned)type > XG_W64_UNIFORM_F64) return fail(XG_EINVAL, "unknown output type");
+    if (nstreams == 0 || nstreams > c->n) nstreams = c->n;
+    if (n_per_stream == 0) return fail(XG_EINVAL, "n_per_stream must be positive");
+    uint64_t nt = std::min<uint64_t>(n_per_stream, std::max<uint64_t>(128, (uint64_t(1) << 26) / nstreams));
+    nt = align_up(nt, 32);
+    std::lock_guard<std::mutex> lk(c->mu);
+    void* saved = nullptr;
+    void* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (saved) {
+            cudaMemcpyAsync(c->state_mem, saved, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+            cudaStreamSynchronize(c->stream);
+            cudaFree(saved);
+        }
+        if (out) cudaFree(out);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&saved, c->state_bytes);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(saved, c->state_mem, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)nstreams * nt * 8);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return cuda_fail(e, "autotune set-up");
+    }
+    static const int kBlocks[] = {32, 64, 128, 256};
+    int best_cfg = -1, best_block = 0;
+    float best = 1e30f;
+    xg_status st = XG_OK;
+    for (int ci = 0; ci < xg64::kNumCfgs && st == XG_OK; ++ci) {
+        for (int b : kBlocks) {
+            st = enqueue(c, type, 0, nstreams, nt, out, nt, ci, b);
+            if (st != XG_OK) break;
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 3 && st == XG_OK; ++r) st = enqueue(c, type, 0, nstreams, nt, out, nt, ci, b);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = cuda_fail(cudaGetLastError(), "autotune timing");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3.f;
+            if (ms < best) {
+                best = ms;
+                best_cfg = ci;
+                best_block = b;
+            }
+        }
+    }
+    cleanup();
+    if (st != XG_OK) return st;
+    c->cfg[type] = best_cfg;
+    c->blk[type] = best_block;
+    if (tpg) *tpg = (uint32_t)xg64::kCfgs[best_cfg].tpg;
+    if (wpl) *wpl = (uint32_t)xg64::kCfgs[best_cfg].wpl;
+    if (block) *block = (uint32_t)best_block;
+    if (best_ms) *best_ms = best;
+    return XG_OK;
+}
+
+}  // extern "C"

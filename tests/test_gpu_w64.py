@@ -1,0 +1,126 @@
+"""64-bit-word generators on the GPU against the 64-bit oracle: raw u64
+outputs and FP64 uniforms bit-exact, for every launch shape, ragged lengths,
+split calls, state save/restore, host outputs and the bench's full size
+(sampled rows)."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1108_0486_gb300 import api as A
+    return A
+
+
+def _u(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def test_parameter_set_matches_oracle(api):
+    params, omega = api.Streams64.params()
+    assert params == O.PARAM_SET_W64
+    assert omega == O.omega64()
+
+
+@pytest.mark.parametrize("launch", [(4, 8), (8, 4), (16, 2), (32, 1)])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 1000, 4099])
+def test_u64_and_uniform_bit_exact(api, launch, n):
+    seeds = list(range(100, 137))
+    st = api.Streams64(len(seeds), seeds=seeds)
+    st.set_launch("u64", *launch)
+    st.set_launch("uniform", *launch)
+    got = _u(st.u64(n))
+    assert np.array_equal(got, O.streams64(seeds, n))
+    # the streams continue: next n as uniforms equal the oracle's words n..2n
+    gu = st.uniform(n).cpu().numpy()
+    ref = O.streams64(seeds, 2 * n)[:, n:]
+    assert np.array_equal(gu, O.uniform64_of(ref).reshape(gu.shape))
+
+
+def test_weyl_off_is_the_raw_recurrence(api):
+    seeds = [7, 8, 9]
+    st = api.Streams64(3, weyl=False, seeds=seeds)
+    got = _u(st.u64(777))
+    for i, s in enumerate(seeds):
+        g = O.Xorgens64(*O.PARAM_SET_W64, weyl=False).seed(s)
+        assert np.array_equal(got[i], g.raw(777))
+
+
+def test_split_calls_concatenate(api):
+    seeds = list(range(1, 65))
+    rng = np.random.default_rng(9)
+    cuts = sorted(int(v) for v in rng.integers(1, 5000, 6))
+    st = api.Streams64(64, seeds=seeds)
+    pieces, prev = [], 0
+    for k, c in enumerate(cuts + [5000]):
+        if c == prev:
+            continue
+        kind = "u64" if k % 2 == 0 else "uniform"
+        t = st.generate(kind, c - prev)
+        pieces.append(("u64" if kind == "u64" else "f64", t.cpu().numpy()))
+        prev = c
+    ref = O.streams64(seeds, 5000)
+    off = 0
+    for kind, arr in pieces:
+        w = arr.shape[1]
+        if kind == "u64":
+            assert np.array_equal(arr.view(np.uint64), ref[:, off:off + w])
+        else:
+            assert np.array_equal(arr, O.uniform64_of(ref[:, off:off + w]).reshape(arr.shape))
+        off += w
+
+
+def test_state_roundtrip_and_oracle_state(api):
+    st = api.Streams64(4, seeds=[11, 12, 13, 14])
+    st.u64(1234)
+    ring, w = st.get_state(2)
+    g = O.Xorgens64(*O.PARAM_SET_W64).seed(13)
+    g.u64(1234)
+    x, wo = g.get_state()
+    assert np.array_equal(ring, x) and w == wo
+    nxt = _u(st.u64(300, first=2, count=1))[0]
+    st.set_state(2, ring, w)
+    again = _u(st.u64(300, first=2, count=1))[0]
+    assert np.array_equal(nxt, again) and np.array_equal(nxt, g.u64(300))
+
+
+def test_host_output_matches_device(api):
+    seeds = list(range(40, 48))
+    a = api.Streams64(8, seeds=seeds)
+    b = api.Streams64(8, seeds=seeds)
+    dev = _u(a.u64(3001))
+    host = np.zeros((8, 3001), dtype=np.uint64)
+    from paper_1108_0486_gb300 import _lib as L
+    L.xg_w64_generate_u64(b.ctx, 0, 8, 3001, host.ctypes.data, 3001)
+    assert np.array_equal(dev, host)
+
+
+def test_full_size_sampled_rows(api):
+    """16384 streams x 2^16 words (the bench's 64-bit row), autotuned launch:
+    whole rows of sampled streams bit-exact with the oracle."""
+    n_streams, n = 16384, 1 << 16
+    seeds = np.arange(1, n_streams + 1, dtype=np.uint32)
+    st = api.Streams64(n_streams, seeds=seeds)
+    st.autotune("uniform", n)
+    out = st.uniform(n)
+    for row in (0, 1, 4095, 8191, 16383):
+        ref = O.uniform64_of(O.streams64([int(seeds[row])], n)[0])
+        assert np.array_equal(out[row].cpu().numpy(), ref), row
+
+
+def test_argument_errors(api):
+    from paper_1108_0486_gb300 import _lib as L
+    st = api.Streams64(4, seeds=[1, 2, 3, 4])
+    with pytest.raises(L.XGError):
+        st.set_launch("u64", 8, 8)
+    with pytest.raises(L.XGError):
+        st.u64(10, first=3, count=2)
+    buf = torch.empty(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(L.XGError):   # 4-byte aligned, not 8: refused on the host
+        L.xg_w64_generate_u64(st.ctx, 0, 1, 4, buf.data_ptr() + 4, 4)
