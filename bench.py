@@ -51,7 +51,7 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic():
+def _traffic(kernel=None):
     """ncu DRAM bytes per launch of the dominant kernel, if recorded for the
     current kernel sources (else None)."""
     import hashlib
@@ -64,6 +64,8 @@ def _traffic():
         src = b"".join(open(os.path.join(ROOT, "paper_1108_0486_gb300", "csrc", f), "rb").read()
                        for f in ("xg_device.cuh", "xg_kernels.cuh"))
         if hashlib.sha256(src).hexdigest()[:16] != rec.get("kernel_sources_sha256_16"):
+            return None
+        if kernel is not None and rec.get("kernel") != kernel:
             return None
         return float(rec["traffic_bytes_per_launch"])
     except Exception:
@@ -302,7 +304,7 @@ def run_ours(args):
     achieved = bytes_per_launch / (dom_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": args.traffic if args.traffic is not None else _traffic(),
+                "traffic": args.traffic if args.traffic is not None else _traffic(dom_name),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "per_kernel_ms": {"u32": avg_u, "uniform": avg_f}}
 
@@ -311,6 +313,7 @@ def run_ours(args):
         rows = extra_rows(st, stream, torch, peak)
         rows["batched"] = batched_row(torch, L, stream, peak)
         rows["serving"] = serving_row(torch, L, stream, seconds=args.serve_seconds)
+        rows["serving_sweep"] = serving_sweep(torch, L, stream)
         try:
             rows["curand_xorwow_context"] = curand_row(torch, stream)
         except Exception as e:  # context only: never fail the bench on it
@@ -384,14 +387,14 @@ def extra_rows(st, stream, torch, peak):
     n64 = N_PER
     b64 = torch.empty((STREAMS, n64), dtype=torch.float64, device="cuda")
     tuned64 = s64.autotune("uniform", n64)
-    s64.autotune("u64", n64)
+    tuned64u = s64.autotune("u64", n64)
     ms_f = _time(lambda: s64.uniform(n64, out=b64), stream, torch)
     ms_u = _time(lambda: s64.u64(n64, out=b64.view(torch.int64)), stream, torch)
     rn64 = STREAMS * n64
     rows["w64_uniform_f64"] = {"rn_s": rn64 / (ms_f / 1e3), "ms": ms_f,
                                "hbm_frac": rn64 * 8 / (ms_f / 1e3) / 1e9 / peak, "launch": tuned64}
     rows["w64_u64"] = {"rn_s": rn64 / (ms_u / 1e3), "ms": ms_u,
-                       "hbm_frac": rn64 * 8 / (ms_u / 1e3) / 1e9 / peak}
+                       "hbm_frac": rn64 * 8 / (ms_u / 1e3) / 1e9 / peak, "launch": tuned64u}
     s64.close()
     del b64
     return rows
@@ -526,6 +529,21 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0,
     return row
 
 
+def serving_sweep(torch, L, stream, rates=(40000.0, 160000.0, 320000.0, 640000.0), seconds=0.5):
+    """Saturation sweep of the serving row: the same request mix at higher
+    Poisson rates.  Reports, per rate, what was delivered and the latency;
+    'submit_rate' is the rate the single host submitter actually achieved
+    (the host-side bound of this setup)."""
+    out = []
+    for rate in rates:
+        r = serving_row(torch, L, stream, seconds=seconds, rate=rate, plain=False)
+        out.append({"offered_req_s": rate, "submit_rate": r["requests"] / r["wall_s"],
+                    "delivered_rn_s": r["rn_s"], "offered_rn_s": r["offered_rn_s"],
+                    "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "max_ms": r["max_ms"],
+                    "mean_batch": r["mean_batch"], "refused_retries": r["refused_retries"]})
+    return out
+
+
 def curand_row(torch, stream, n=1 << 30):
     """Context only: NVIDIA's XORWOW generator (the CURAND row of the paper's
     Table 1) timed through the cuRAND host API on the same GPU, 2^30 u32 and
@@ -611,9 +629,10 @@ def profile_kernel(args):
         from paper_1108_0486_gb300 import Streams64
         st = Streams64(STREAMS, seeds=W.seeds(STREAMS), stream=stream)
         if args.launch:
-            tpg, wpl = (int(v) for v in args.launch.split(","))
-            st.set_launch("uniform", tpg, wpl)
-            out["launch"] = {"tpg": tpg, "wpl": wpl, "block": "default of the configuration"}
+            v = [int(x) for x in args.launch.split(",")]
+            block = v[2] if len(v) > 2 else 0
+            st.set_launch("uniform", v[0], v[1], block)
+            out["launch"] = {"tpg": v[0], "wpl": v[1], "block": block or "default of the configuration"}
         elif not args.no_autotune:
             out["launch"] = st.autotune("uniform", n)
         buf = torch.empty((STREAMS, n), dtype=torch.float64, device="cuda")
@@ -646,7 +665,8 @@ def main():
     ap.add_argument("--n-per", type=int, default=None,
                     help="override words per stream (profiling of a smaller case; not a bench line)")
     ap.add_argument("--launch", default=None,
-                    help="profiling case: fixed lanes,words per lane (e.g. 8,4) instead of autotuning")
+                    help="profiling case: fixed lanes,words per lane[,block] (e.g. 8,4) instead of autotuning "
+                         "(the block applies to the 64-bit case)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
     args = ap.parse_args()

@@ -80,6 +80,11 @@ xg_status xg_w64_generate_u64(xg_w64_ctx* ctx, uint32_t first, uint32_t nstreams
 xg_status xg_w64_generate_uniform_f64(xg_w64_ctx* ctx, uint32_t first, uint32_t nstreams,
                                       uint64_t n_per_stream, double* out, uint64_t ld);
 
+/* The FP64 uniform conversion alone: d_out[i] = (d_words[i] >> 11) * 2^-53
+ * for n given 64-bit words (device memory, 8-byte aligned; may not overlap).
+ * Asynchronous. */
+xg_status xg_w64_transform_uniform_f64(xg_w64_ctx* ctx, const uint64_t* d_words, uint64_t n, double* d_out);
+
 /* Launch shape per output type: tpg lanes per stream x wpl words per lane,
  * tpg * wpl = 32: (4,8) (8,4) (16,2) (32,1); (0,0) restores the automatic
  * choice.  block 0 = the configuration's default threads per block. */

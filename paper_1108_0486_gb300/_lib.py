@@ -102,6 +102,7 @@ SIGNATURES = {
     "xg_w64_set_state": [vp, u32, vp, u64],
     "xg_w64_generate_u64": [vp, u32, u32, u64, vp, u64],
     "xg_w64_generate_uniform_f64": [vp, u32, u32, u64, vp, u64],
+    "xg_w64_transform_uniform_f64": [vp, vp, u64, vp],
     "xg_w64_set_launch": [vp, i32, u32, u32, u32],
     "xg_w64_autotune": [vp, i32, u32, u64, P_u32, P_u32, P_u32, ctypes.POINTER(ctypes.c_float)],
 }
@@ -356,6 +357,11 @@ def xg_w64_generate_u64(ctx, first, nstreams, n_per_stream, out_ptr, ld) -> None
 def xg_w64_generate_uniform_f64(ctx, first, nstreams, n_per_stream, out_ptr, ld) -> None:
     call("xg_w64_generate_uniform_f64", ctypes.c_void_p(ctx), first, nstreams, n_per_stream,
          ctypes.c_void_p(out_ptr), ld)
+
+
+def xg_w64_transform_uniform_f64(ctx, words_ptr, n, out_ptr) -> None:
+    call("xg_w64_transform_uniform_f64", ctypes.c_void_p(ctx), ctypes.c_void_p(words_ptr), n,
+         ctypes.c_void_p(out_ptr))
 
 
 def xg_w64_set_launch(ctx, out_type, tpg, wpl, block=0) -> None:

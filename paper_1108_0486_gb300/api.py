@@ -330,3 +330,9 @@ class Streams64:
 
     def generate(self, kind: str, n: int, **kw):
         return {"u64": self.u64, "uniform": self.uniform}[kind](n, **kw)
+
+    def transform_uniform(self, words: torch.Tensor, out=None):
+        """FP64 uniforms of given 64-bit words (an int64 device tensor)."""
+        out = torch.empty(words.numel(), dtype=torch.float64, device="cuda") if out is None else out
+        L.xg_w64_transform_uniform_f64(self.ctx, words.data_ptr(), words.numel(), out.data_ptr())
+        return out

@@ -270,6 +270,18 @@ xg_status xg_w64_generate_uniform_f64(xg_w64_ctx* c, uint32_t first, uint32_t ns
     return generate(c, xg64::kUniformF64, first, nstreams, n, out, ld);
 }
 
+xg_status xg_w64_transform_uniform_f64(xg_w64_ctx* c, const uint64_t* d_words, uint64_t n, double* d_out)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if (n == 0) return XG_OK;
+    if (!d_words || !d_out) return fail(XG_EINVAL, "null pointer");
+    if ((reinterpret_cast<uintptr_t>(d_words) | reinterpret_cast<uintptr_t>(d_out)) & 7u)
+        return fail(XG_EINVAL, "buffers must be 8-byte aligned");
+    cudaError_t e = xg64::launch_transform_uniform(d_words, n, reinterpret_cast<uint64_t*>(d_out), c->sm_count,
+                                                   c->stream);
+    return e == cudaSuccess ? XG_OK : cuda_fail(e, "64-bit transform_uniform");
+}
+
 xg_status xg_w64_set_launch(xg_w64_ctx* c, xg_w64_type type, uint32_t tpg, uint32_t wpl, uint32_t block)
 {
     if (!c) return fail(XG_EINVAL, "null context");

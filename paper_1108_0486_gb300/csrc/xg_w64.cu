@@ -63,7 +63,7 @@ __device__ __forceinline__ uint64_t combine(uint64_t x, uint64_t w)
 // is 2^(p - 53) (1 + f), so the biased exponent is 1023 + p - 53 and the 52
 // fraction bits are m shifted left by 52 - p with the leading one dropped.
 // (FP64 arithmetic is a narrow pipe on this part; this needs none.)
-__device__ __forceinline__ uint64_t to_uniform_bits(uint64_t o)
+__device__ __noinline__ uint64_t to_uniform_bits_any(uint64_t o)
 {
     const uint64_t m = o >> 11;
     if (m == 0) return 0;
@@ -71,6 +71,24 @@ __device__ __forceinline__ uint64_t to_uniform_bits(uint64_t o)
     const int p = 63 - lz;
     const uint64_t frac = (m << (52 - p)) & ((uint64_t(1) << 52) - 1);
     return ((uint64_t)(1023 + p - 53) << 52) | frac;
+}
+
+// The same on 32-bit halves.  When m = mh:ml has its leading one in mh (all
+// but 2^-21 of the words), lz = clz(mh) is 11..31 and the normalising shift
+// k = lz - 11 is below 32, so m << k is two funnel shifts; the leading one
+// (bit 52) is then added into the exponent field, whose value before the
+// carry is 1033 - lz - 1.  Other words take the general path above.
+__device__ __forceinline__ uint64_t to_uniform_bits(uint64_t o)
+{
+    const uint32_t oh = (uint32_t)(o >> 32), ol = (uint32_t)o;
+    const uint32_t mh = oh >> 11;
+    const uint32_t ml = __funnelshift_r(ol, oh, 11);
+    if (mh == 0) return to_uniform_bits_any(o);
+    const int lz = __clz(mh);
+    const int k = lz - 11;
+    const uint32_t hi = __funnelshift_l(ml, mh, k) + ((uint32_t)(1032 - lz) << 20);
+    const uint32_t lo = ml << k;
+    return ((uint64_t)hi << 32) | lo;
 }
 
 template <int TPG, int WPL>
@@ -345,6 +363,25 @@ cudaError_t launch_gen(int cfg, int kind, bool vec, int block, const GenArgs& a,
     case 3: return launch_cfg<32, 1>(kind, vec, block, a, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// FP64 uniform conversion of n given words (grid-stride).
+__global__ void __launch_bounds__(256) transform_uniform_kernel(const uint64_t* __restrict__ in, uint64_t n,
+                                                                 uint64_t* __restrict__ out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = to_uniform_bits(in[i]);
+}
+
+cudaError_t launch_transform_uniform(const uint64_t* in, uint64_t n, uint64_t* out, int sms, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int block = 256;
+    uint64_t grid = (n + block - 1) / block;
+    if (grid > (uint64_t)sms * 16) grid = (uint64_t)sms * 16;
+    transform_uniform_kernel<<<(unsigned)grid, block, 0, s>>>(in, n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_seed(const State& st, const uint32_t* d_seeds, uint32_t first, uint32_t count,

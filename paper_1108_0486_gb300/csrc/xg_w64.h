@@ -55,5 +55,6 @@ int cfg_index(int tpg, int wpl);
 cudaError_t launch_seed(const State& st, const uint32_t* d_seeds, uint32_t first, uint32_t count,
                         cudaStream_t s);
 cudaError_t launch_gen(int cfg, int kind, bool vec, int block, const GenArgs& a, cudaStream_t s);
+cudaError_t launch_transform_uniform(const uint64_t* in, uint64_t n, uint64_t* out, int sms, cudaStream_t s);
 
 }  // namespace xg64

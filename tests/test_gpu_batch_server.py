@@ -372,3 +372,30 @@ def test_collect_drains_finished_requests():
         assert all(g[1] <= g[2] <= g[3] for g in got)  # submit <= launch <= done
         assert srv.stats()["outstanding_bytes"] == 0
         srv.stop()
+
+
+def test_server_serving_workload_sampled():
+    """The serving workload's request generator (65536 streams, sizes
+    log-uniform in [2^10, 2^22], 60/30/10 normal/uniform/u32, PCG64 seed 486)
+    over a 0.05 s window (~1000 requests, ~2 GB), submitted back to back into
+    the library pool; every 50th request (a 2% sample) is checked against the
+    oracle with its stream advanced by the earlier requests on it."""
+    S = 65536
+    reqs = W.serving_requests(n_streams=S, rate=20000.0, duration=0.05)
+    seeds = W.seeds(S)
+    with Streams(S, seeds=seeds) as st:
+        srv = st.serve(mem_cap_bytes=16 << 30)
+        tickets = [srv.submit(r.stream, r.kind, r.count) for r in reqs]
+        sample = list(range(0, len(reqs), 50))
+        got = {i: srv.result(tickets[i], reqs[i].kind, reqs[i].count).clone() for i in sample}
+        for t in tickets:
+            srv.wait(t, 60000)
+            srv.release(t)
+        srv.stop()
+    assert len(reqs) > 500 and len(sample) >= 10
+    for i in sample:
+        r = reqs[i]
+        k = KINDS[r.kind]
+        before = sum(nwords(KINDS[q.kind], q.count) for q in reqs[:i] if q.stream == r.stream)
+        words = O.Xorgens.param_set(0).seed(int(seeds[r.stream])).u32(before + nwords(k, r.count))
+        check(k, got[i][:r.count], oracle_call(words[before:], k, r.count))

@@ -114,6 +114,21 @@ def test_full_size_sampled_rows(api):
         assert np.array_equal(out[row].cpu().numpy(), ref), row
 
 
+def test_uniform_conversion_edge_words(api):
+    """The conversion alone on words that take each path of the kernel's
+    integer construction (leading one in either half, zero, extremes)."""
+    edge = [0, 1, (1 << 11) - 1, 1 << 11, (1 << 11) + 1, (1 << 43) - 1, 1 << 43, (1 << 43) + 1,
+            (1 << 44) - 1, 1 << 63, (1 << 64) - 1, 0x9E3779B97F4A7C15]
+    edge += [1 << j for j in range(64)] + [(1 << j) - 1 for j in range(1, 65)]
+    rng = np.random.default_rng(12)
+    rand = rng.integers(0, 2**64 - 1, 100000, dtype=np.uint64, endpoint=True)
+    small = rand >> rng.integers(0, 64, rand.size, dtype=np.uint64)
+    words = np.concatenate([np.array(edge, dtype=np.uint64), rand, small])
+    st = api.Streams64(1)
+    got = st.transform_uniform(torch.from_numpy(words.view(np.int64)).cuda()).cpu().numpy()
+    assert np.array_equal(got, O.uniform64_of(words))
+
+
 def test_argument_errors(api):
     from paper_1108_0486_gb300 import _lib as L
     st = api.Streams64(4, seeds=[1, 2, 3, 4])
