@@ -414,16 +414,33 @@ def batched_row(torch, L, stream, peak, reps=3):
     st = Streams(len(items), seeds=seeds, stream=stream)
     spec = [(it.stream, it.kind, it.count, o.data_ptr()) for it, o in zip(items, outs)]
     arr = L.make_items(spec)  # built once, outside the timed region
-    ms = _time(lambda: L.xg_generate_batch(st.ctx, arr), stream, torch, reps=reps, warm=1)
+    # two warm-up calls: calls alternate between two launchers (so that one
+    # can be planned while the other runs), and each sizes its buffers once
+    ms = _time(lambda: L.xg_generate_batch(st.ctx, arr), stream, torch, reps=reps, warm=2)
+    # host time of the call itself (planning and enqueueing; the GPU is idle
+    # for the part of it before the first kernel is enqueued)
+    host = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.xg_generate_batch(st.ctx, arr)
+        host.append((time.perf_counter() - t0) * 1e3)
+    torch.cuda.synchronize()
+    by_piece = {}
+    for q in (18, 19, 20):
+        st.set_batch_split(1 << q)
+        by_piece[f"2^{q}"] = _time(lambda: L.xg_generate_batch(st.ctx, arr), stream, torch, reps=reps, warm=2)
+    st.set_batch_split(0)
     longest = max(range(len(items)), key=lambda i: items[i].count)
     one = L.make_items([spec[longest]])
-    ms_long = _time(lambda: L.xg_generate_batch(st.ctx, one), stream, torch, reps=reps, warm=1)
+    ms_long = _time(lambda: L.xg_generate_batch(st.ctx, one), stream, torch, reps=reps, warm=2)
     st.close()
     del outs
     torch.cuda.empty_cache()
     return {"workload": "4096 items (streams 0..4095, seeds 1..4096), lengths log-uniform [2^10, 2^24] "
                         "(PCG64 seed 1108), types uniform over u32/uniform/normal, one graph-replayed launch",
-            "rns_total": total, "ms": ms, "rn_s": total / (ms / 1e3),
+            "rns_total": total, "ms": ms, "rn_s": total / (ms / 1e3), "host_call_ms": min(host),
+            "ms_by_forced_piece_len": by_piece,
             "hbm_frac": total * 4 / (ms / 1e3) / 1e9 / peak,
             "longest_item": items[longest].count, "longest_item_alone_ms": ms_long,
             "hbm_floor_ms": total * 4 / peak / 1e6}

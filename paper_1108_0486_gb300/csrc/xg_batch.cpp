@@ -24,10 +24,13 @@ static uint64_t cost_of(uint32_t kind, uint64_t words)
     return words * (kind == kNormal ? 18u : kind == kUniform ? 9u : 8u);
 }
 
-void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan)
+// Units and pieces of a batch, chains linked, one cost per chain head; the
+// heads are not yet ordered (plan_order does that).
+static void plan_units(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan)
 {
     plan.units.clear();
     plan.heads.clear();
+    plan.chain_words.clear();
     plan.pieces.clear();
     plan.piece_stream.clear();
     plan.piece_skip.clear();
@@ -48,10 +51,21 @@ void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t 
     auto& last = plan.last_unit;
     auto& chain = plan.chain_of;
     for (uint32_t i = 0; i < n; ++i) ++count[items[i].stream];
-    plan.units.reserve(n);
-    plan.heads.reserve(n);
-    std::vector<uint64_t> words;
-    words.reserve(n);
+    size_t npieces_all = 0;
+    if (piece_len) {
+        for (uint32_t i = 0; i < n; ++i) {
+            const uint64_t w = words_of(items[i].kind, items[i].count);
+            if (count[items[i].stream] == 1 && w >= 2 * piece_len) npieces_all += (w + piece_len - 1) / piece_len;
+        }
+    }
+    plan.units.reserve(n + npieces_all);
+    plan.heads.reserve(n + npieces_all);
+    plan.chain_words.reserve(n + npieces_all);
+    plan.pieces.reserve(npieces_all);
+    plan.piece_stream.reserve(npieces_all);
+    plan.piece_skip.reserve(npieces_all);
+    plan.piece_index.reserve(npieces_all);
+    auto& words = plan.chain_words;  // cost per head, in head order until plan_order
     for (uint32_t i = 0; i < n; ++i) {
         const HostItem& h = items[i];
         const uint64_t w = words_of(h.kind, h.count);
@@ -94,17 +108,51 @@ void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t 
         last[items[i].stream] = 0;
         chain[items[i].stream] = 0;
     }
-    std::vector<uint32_t> order(plan.heads.size());
-    std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t a, uint32_t b) { return words[a] > words[b]; });
-    std::vector<uint32_t> sorted(plan.heads.size());
-    plan.chain_words.resize(plan.heads.size());
-    for (size_t k = 0; k < order.size(); ++k) {
-        sorted[k] = plan.heads[order[k]];
-        plan.chain_words[k] = words[order[k]];
+}
+
+// Order the chain heads costliest first by a counting sort on the cost
+// rounded down to 7 significant bits (exponent and 6 bits below the leading
+// one: within 1.6% of the exact order); equal keys keep submission order.
+// Linear in the number of heads, which runs to tens of thousands when long
+// calls are cut.
+static uint32_t cost_key(uint64_t c)
+{
+    if (c < 64) return (uint32_t)c;
+    const int e = 63 - __builtin_clzll(c);               // 6 .. 63
+    return (uint32_t)((e - 5) << 6) | (uint32_t)((c >> (e - 6)) & 63u);
+}
+
+static void plan_order(BatchPlan& plan)
+{
+    constexpr uint32_t kKeys = 59u << 6;   // cost_key < 58 * 64 + 64
+    const size_t nh = plan.heads.size();
+    std::vector<uint32_t> start(kKeys + 1, 0u);
+    std::vector<uint32_t> key(nh);
+    for (size_t k = 0; k < nh; ++k) {
+        key[k] = cost_key(plan.chain_words[k]);
+        ++start[kKeys - 1 - key[k]];   // descending
+    }
+    uint32_t acc = 0;
+    for (uint32_t b = 0; b <= kKeys; ++b) {
+        const uint32_t v = start[b];
+        start[b] = acc;
+        acc += v;
+    }
+    std::vector<uint32_t> sorted(nh);
+    std::vector<uint64_t> cost(nh);
+    for (size_t k = 0; k < nh; ++k) {
+        const uint32_t pos = start[kKeys - 1 - key[k]]++;
+        sorted[pos] = plan.heads[k];
+        cost[pos] = plan.chain_words[k];
     }
     plan.heads.swap(sorted);
+    plan.chain_words.swap(cost);
+}
+
+void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan)
+{
+    plan_units(items, n, piece_len, n_streams, plan);
+    plan_order(plan);
 }
 
 BatchLauncher::~BatchLauncher()
@@ -224,23 +272,20 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
 {
     const uint32_t P = (uint32_t)plan_.pieces.size();
     if (P == 0) return XG_OK;
-    // per step b: (src, dst) piece pairs; pieces of one call are consecutive
-    std::vector<std::vector<uint32_t>> src, dst;
+    // per step b: (src, dst) piece pairs; pieces of one call are consecutive.
+    // Count them per step first, then write the lists straight into staging.
+    uint32_t per_step[32] = {0};
+    int nsteps = 0;
     for (uint32_t k = 0; k < P; ++k) {
         const uint32_t m = plan_.piece_index[k];
         if (m == 0) continue;
-        int b = 31;
-        while (!((m >> b) & 1u)) --b;
-        if ((int)src.size() <= b) {
-            src.resize(b + 1);
-            dst.resize(b + 1);
-        }
-        src[b].push_back(k - (1u << b));
-        dst[b].push_back(k);
+        const int b = 31 - __builtin_clz(m);
+        ++per_step[b];
+        nsteps = std::max(nsteps, b + 1);
     }
     size_t npairs = 0;
-    for (auto& l : src) npairs += l.size();
-    // device buffer: rings | weyls | gather streams | gather skips (zeros) | gather ids | pair lists
+    for (int b = 0; b < nsteps; ++b) npairs += per_step[b];
+    // device buffer: rings | weyls | gather streams | gather skips | pair lists
     const size_t off_rings = 0;
     const size_t off_weyl = off_rings + (size_t)P * 512;
     const size_t off_streams = (off_weyl + (size_t)P * 4 + 15) / 16 * 16;
@@ -254,28 +299,35 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
     char* db = static_cast<char*>(d_jbuf_);
     // every piece's Weyl word comes from the gather (its own skip); its ring
     // from the gather (m = 0) or a doubling step
-    for (uint32_t k = 0; k < P; ++k) {
-        reinterpret_cast<uint32_t*>(hb + off_streams)[k] = plan_.piece_stream[k];
-        reinterpret_cast<uint64_t*>(hb + off_skip)[k] = plan_.piece_skip[k];
-    }
-    std::vector<size_t> src_off(src.size()), dst_off(src.size());
+    std::memcpy(hb + off_streams, plan_.piece_stream.data(), (size_t)P * 4);
+    std::memcpy(hb + off_skip, plan_.piece_skip.data(), (size_t)P * 8);
+    size_t src_off[32], dst_off[32];
+    uint32_t* src_w[32];
+    uint32_t* dst_w[32];
     size_t o = off_lists;
-    for (size_t b = 0; b < src.size(); ++b) {
+    for (int b = 0; b < nsteps; ++b) {
         src_off[b] = o;
-        std::memcpy(hb + o, src[b].data(), src[b].size() * 4);
-        o += src[b].size() * 4;
+        src_w[b] = reinterpret_cast<uint32_t*>(hb + o);
+        o += (size_t)per_step[b] * 4;
         dst_off[b] = o;
-        std::memcpy(hb + o, dst[b].data(), dst[b].size() * 4);
-        o += dst[b].size() * 4;
+        dst_w[b] = reinterpret_cast<uint32_t*>(hb + o);
+        o += (size_t)per_step[b] * 4;
+    }
+    for (uint32_t k = 0; k < P; ++k) {
+        const uint32_t m = plan_.piece_index[k];
+        if (m == 0) continue;
+        const int b = 31 - __builtin_clz(m);
+        *src_w[b]++ = k - (1u << b);
+        *dst_w[b]++ = k;
     }
     for (uint32_t k = 0; k < P; ++k) {
         plan_.pieces[k].ring = reinterpret_cast<const uint32_t*>(db + off_rings + (size_t)k * 512);
         plan_.pieces[k].weyl0 = reinterpret_cast<const uint32_t*>(db + off_weyl + (size_t)k * 4);
     }
     // matrices first (the first use builds them and synchronises)
-    std::vector<const uint64_t*> mats(src.size(), nullptr);
-    for (size_t b = 0; b < src.size(); ++b) {
-        if (src[b].empty()) continue;
+    const uint64_t* mats[32] = {nullptr};
+    for (int b = 0; b < nsteps; ++b) {
+        if (per_step[b] == 0) continue;
         xg_status st = XG_OK;
         mats[b] = jump_matrix(c->device, (int)c->param_set, plan_.split_log2 + (int)b, s, &st);
         if (!mats[b]) return st;
@@ -290,12 +342,12 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
                             reinterpret_cast<uint32_t*>(db + off_weyl), 1u, c->weyl_on ? 0x9E3779B9u : 0u,
                             s) != cudaSuccess)
         return XG_ECUDA;
-    for (size_t b = 0; b < src.size(); ++b) {
-        if (src[b].empty()) continue;
+    for (int b = 0; b < nsteps; ++b) {
+        if (per_step[b] == 0) continue;
         if (zero_rings(reinterpret_cast<uint32_t*>(db + off_rings), reinterpret_cast<const uint32_t*>(db + dst_off[b]),
-                       (uint32_t)dst[b].size(), s) != cudaSuccess)
+                       per_step[b], s) != cudaSuccess)
             return XG_ECUDA;
-        if (launch_gf2_apply_pairs(mats[b], reinterpret_cast<uint32_t*>(db + off_rings), (uint32_t)src[b].size(),
+        if (launch_gf2_apply_pairs(mats[b], reinterpret_cast<uint32_t*>(db + off_rings), per_step[b],
                                    reinterpret_cast<const uint32_t*>(db + src_off[b]),
                                    reinterpret_cast<const uint32_t*>(db + dst_off[b]), c->sm_count, s) != cudaSuccess)
             return XG_ECUDA;
@@ -310,10 +362,13 @@ xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cu
         if (xg_status st = reserve(c, std::max<uint32_t>(n, 64))) return st;
     }
     if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
-    plan_batch(items, n, choose_piece_len(c, items, n), c->n, plan_);
+    // the jump prologue needs only the pieces: enqueue it before ordering the
+    // heads, so that the GPU starts while the host finishes the plan
+    plan_units(items, n, choose_piece_len(c, items, n), c->n, plan_);
     const uint32_t nu = (uint32_t)plan_.units.size();
     if (xg_status st = reserve(c, nu)) return st;
     if (xg_status st = prologue(c, s)) return st;
+    plan_order(plan_);
     if (units_per_item) std::memcpy(units_per_item, plan_.units_per_item.data(), (size_t)n * 4);
     char* base = static_cast<char*>(h_staging_);
     BatchHeader hdr{0u, (uint32_t)plan_.heads.size(), nu, capacity_};
