@@ -546,19 +546,97 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0,
     return row
 
 
-def serving_sweep(torch, L, stream, rates=(40000.0, 160000.0, 320000.0, 640000.0), seconds=0.5):
-    """Saturation sweep of the serving row: the same request mix at higher
-    Poisson rates.  Reports, per rate, what was delivered and the latency;
-    'submit_rate' is the rate the single host submitter actually achieved
-    (the host-side bound of this setup)."""
-    out = []
-    for rate in rates:
-        r = serving_row(torch, L, stream, seconds=seconds, rate=rate, plain=False)
-        out.append({"offered_req_s": rate, "submit_rate": r["requests"] / r["wall_s"],
-                    "delivered_rn_s": r["rn_s"], "offered_rn_s": r["offered_rn_s"],
-                    "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "max_ms": r["max_ms"],
-                    "mean_batch": r["mean_batch"], "refused_retries": r["refused_retries"]})
-    return out
+def serving_bulk(torch, L, stream, rate, seconds, lanes=48, max_batch=1024, split=0, cap_gib=16, size_scale=1):
+    """Open-loop Poisson arrivals at `rate`, the serving row's mix, submitted
+    by one host thread in bulk (xg_submit_many: every request that has
+    arrived by the time of the call), library pool outputs released by a
+    reaper that drains completions in bulk.  Latency = completion minus
+    arrival, both on CLOCK_MONOTONIC (the server's clock)."""
+    import threading as th
+    from paper_1108_0486_gb300 import Streams
+    S = 65536
+    reqs = W.serving_requests(n_streams=S, rate=rate, duration=seconds, lo=(1 << 10) * size_scale,
+                              hi=(1 << 22) * size_scale)
+    n = len(reqs)
+    rec = L.make_requests([(r.stream, r.kind, r.count, 0) for r in reqs])
+    arrival = np.array([r.t_arrival for r in reqs])
+    tickets = np.zeros(n, dtype=np.uint64)
+    st = Streams(S, seeds=W.seeds(S), stream=stream)
+    torch.cuda.synchronize()
+    if split:
+        st.set_batch_split(split)
+    L.xg_server_start(st.ctx, cap_gib << 30, max_batch, lanes)
+    done = np.zeros(n, dtype=np.uint64)          # completion time per ticket order
+    tick_done = np.zeros(n, dtype=np.uint64)
+    got = [0]
+    buf = np.zeros(65536, dtype=L.COMPLETION_DTYPE)
+
+    collect_s = [0.0]
+
+    def reaper():
+        while got[0] < n:
+            c0 = time.perf_counter()
+            k = L.xg_collect_into(st.ctx, buf, release=True)
+            collect_s[0] += time.perf_counter() - c0
+            if k:
+                tick_done[got[0]:got[0] + k] = buf["ticket"][:k]
+                done[got[0]:got[0] + k] = buf["t_done_ns"][:k]
+                got[0] += k
+            else:
+                time.sleep(0.0001)
+
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(1e-4)
+    rt = th.Thread(target=reaper)
+    rt.start()
+    refused = 0
+    calls = 0
+    submit_s = 0.0
+    t0 = time.monotonic_ns()
+    i = 0
+    while i < n:
+        now = (time.monotonic_ns() - t0) / 1e9
+        j = int(np.searchsorted(arrival, now, side="right"))
+        if j > i:
+            c0 = time.perf_counter()
+            acc = L.xg_submit_many(st.ctx, rec, i, j - i, tickets)
+            submit_s += time.perf_counter() - c0
+            calls += 1
+            if acc < j - i:
+                refused += 1
+                time.sleep(0.0001)
+            i += acc
+        else:
+            time.sleep(max(0.0, min(1e-4, arrival[i] - now)))
+    rt.join()
+    sys.setswitchinterval(old_switch)
+    wall = (time.monotonic_ns() - t0) / 1e9
+    stats = L.xg_server_stats_get(st.ctx)
+    L.xg_server_stop(st.ctx)
+    st.close()
+    # tickets are issued in submission order from the first ticket number
+    base = int(tickets.min())
+    order = (tick_done - base).astype(np.int64)
+    t_done = np.empty(n, dtype=np.float64)
+    t_done[order] = done.astype(np.float64)
+    lat_ms = (t_done - (t0 + arrival * 1e9)) / 1e6
+    words = int(rec["count"].sum())
+    span = (t_done.max() - t0) / 1e9
+    return {"offered_req_s": rate, "window_s": seconds, "requests": n,
+            "submit_calls": calls, "mean_requests_per_call": n / max(1, calls),
+            "delivered_rn_s": words / span, "offered_rn_s": words / seconds,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "max_ms": float(lat_ms.max()), "mean_batch": stats["items_launched"] / max(1, stats["batches"]),
+            "server_thread_launch_busy": stats["host_launch_ns"] / 1e9 / wall,
+            "submit_calls_busy": submit_s / wall, "collect_calls_busy": collect_s[0] / wall,
+            "refused_calls": refused, "wall_s": wall}
+
+
+def serving_sweep(torch, L, stream, rates=(40000.0, 160000.0, 640000.0, 1280000.0, 2560000.0), seconds=0.25):
+    """Saturation sweep of the serving workload with bulk submission:
+    latency (from arrival) and delivered RN/s as the Poisson rate grows past
+    what the GPU can serve."""
+    return [serving_bulk(torch, L, stream, rate, seconds) for rate in rates]
 
 
 def curand_row(torch, stream, n=1 << 30):

@@ -236,14 +236,20 @@ typedef struct {
  * one of the lanes is free launches the oldest ready requests as one batch
  * (one replay of the persistent batch kernel's graph).  Batches on different
  * lanes run concurrently, so requests that arrive while others are on the
- * GPU start as soon as a lane and memory free up.  Each result is identical
+ * GPU start as soon as a lane and memory free up; while the GPU already has
+ * about 1.5 ms of work in flight, new requests wait and gather into larger
+ * batches, and long requests are cut into fewer, longer pieces (jump-ahead
+ * work only pays while the GPU would otherwise idle).  Each result is identical
  * to the same request run alone.  Start-up allocates the pool, each lane's
  * buffers and the jump-ahead powers (about 70 MiB) so that serving itself
  * does not allocate.  A request whose batch fails to launch is
  * reported as XG_EDEVICE by xg_poll / xg_wait and leaves its stream where it
  * was; the server keeps serving.  (For testing that path without a GPU
  * fault, the environment variable XG_INJECT_LAUNCH_FAILURES=N, read at
- * start, makes the first N batch launches fail on the host.) */
+ * start, makes the first N batch launches fail on the host.)  Tracing:
+ * XG_SERVER_TRACE=<path>, read at start, records every batch (lane, items,
+ * units, words, host launch time, GPU time between events around the launch)
+ * and the scheduler loop's time split, written as CSV by xg_server_stop. */
 xg_status xg_server_start(xg_ctx* ctx, const xg_server_config* cfg);
 
 /* Stop the server thread after the batches in flight finish; frees the pool
@@ -253,6 +259,15 @@ xg_status xg_server_stop(xg_ctx* ctx);
 /* Non-blocking.  XG_EAGAIN when admitting the request would put the
  * outstanding output bytes above the cap (retry later, after xg_release). */
 xg_status xg_submit(xg_ctx* ctx, const xg_request* req, uint64_t* ticket);
+
+/* Non-blocking bulk submission: admits reqs[0 .. n) in order, as n calls of
+ * xg_submit would, taking the server's lock once.  tickets[i] receives the
+ * ticket of each admitted request and *n_accepted how many were admitted.
+ * XG_OK when all were; XG_EAGAIN when the cap (or the pool) refused request
+ * *n_accepted, the ones before it staying admitted (resubmit the rest later);
+ * XG_EINVAL, with nothing admitted, when any request is invalid. */
+xg_status xg_submit_many(xg_ctx* ctx, const xg_request* reqs, uint32_t n, uint64_t* tickets,
+                         uint32_t* n_accepted);
 
 /* Non-blocking.  *done = 1 once the request's outputs are in device memory
  * and visible to later work on any stream; *d_result is then its output

@@ -81,6 +81,7 @@ SIGNATURES = {
     "xg_server_start": [vp, vp],
     "xg_server_stop": [vp],
     "xg_submit": [vp, vp, P_u64],
+    "xg_submit_many": [vp, vp, u32, vp, P_u32],
     "xg_poll": [vp, u64, P_i32, P_vp],
     "xg_wait": [vp, u64, u32, P_vp],
     "xg_release": [vp, u64],
@@ -253,6 +254,30 @@ def xg_submit(ctx, stream, out_type, count, d_out=0) -> int:
     return t.value
 
 
+def make_requests(reqs):
+    """A numpy record array laid out as xg_request[] from (stream, type,
+    count, d_out) tuples (build it once, submit slices of it)."""
+    import numpy as np
+    a = np.asarray(reqs, dtype=np.uint64).reshape(-1, 4)
+    rec = np.zeros(a.shape[0], dtype=[("stream", "<u4"), ("type", "<u4"), ("count", "<u8"),
+                                     ("d_out", "<u8")])
+    rec["stream"], rec["type"], rec["count"], rec["d_out"] = a[:, 0], a[:, 1], a[:, 2], a[:, 3]
+    assert rec.itemsize == ctypes.sizeof(XgRequest)
+    return rec
+
+
+def xg_submit_many(ctx, rec, first, n, tickets):
+    """Submit rec[first:first+n] (from make_requests); tickets (numpy uint64)
+    receives their tickets at the same positions.  Returns how many were
+    admitted (an XG_EAGAIN refusal is not raised: fewer than n come back)."""
+    acc = ctypes.c_uint32()
+    st = lib().xg_submit_many(ctypes.c_void_p(ctx), ctypes.c_void_p(rec.ctypes.data + first * rec.itemsize), n,
+                              ctypes.c_void_p(tickets.ctypes.data + first * 8), ctypes.byref(acc))
+    if st not in (XG_OK, XG_EAGAIN):
+        check(st)
+    return acc.value
+
+
 def xg_poll(ctx, ticket):
     done, ptr = ctypes.c_int(), ctypes.c_void_p()
     call("xg_poll", ctypes.c_void_p(ctx), ticket, ctypes.byref(done), ctypes.byref(ptr))
@@ -282,6 +307,20 @@ def xg_collect(ctx, max_n=4096, release=False, buf=None):
     call("xg_collect", ctypes.c_void_p(ctx), arr, len(arr), ctypes.byref(n), int(bool(release)))
     return [(c.ticket, c.t_submit_ns, c.t_launch_ns, c.t_done_ns, c.status, c.d_result)
             for c in arr[: n.value]]
+
+
+COMPLETION_DTYPE = [("ticket", "<u8"), ("t_submit_ns", "<u8"), ("t_launch_ns", "<u8"), ("t_done_ns", "<u8"),
+                    ("status", "<i4"), ("pad", "<u4"), ("d_result", "<u8")]
+
+
+def xg_collect_into(ctx, buf, release=False) -> int:
+    """xg_collect into a numpy record array of COMPLETION_DTYPE; returns the
+    number of records written (no per-record Python objects)."""
+    assert buf.itemsize == ctypes.sizeof(XgCompletion)
+    n = ctypes.c_uint32()
+    call("xg_collect", ctypes.c_void_p(ctx), ctypes.c_void_p(buf.ctypes.data), len(buf), ctypes.byref(n),
+         int(bool(release)))
+    return n.value
 
 
 def xg_server_stats_get(ctx) -> dict:

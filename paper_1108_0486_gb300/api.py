@@ -158,6 +158,19 @@ class Server:
         t = TYPES[kind] if isinstance(kind, str) else int(kind)
         return L.xg_submit(self.ctx, stream, t, count, 0 if out is None else out.data_ptr())
 
+    def submit_many(self, requests, tickets=None):
+        """Submit (stream, kind, count[, out]) tuples in one call; returns the
+        tickets of the admitted ones (all of them unless the cap refused one)."""
+        rows = []
+        for r in requests:
+            k = TYPES[r[1]] if isinstance(r[1], str) else int(r[1])
+            out = r[3] if len(r) > 3 else None
+            rows.append((int(r[0]), k, int(r[2]), 0 if out is None else out.data_ptr()))
+        rec = L.make_requests(rows)
+        t = np.zeros(len(rows), dtype=np.uint64)
+        n = L.xg_submit_many(self.ctx, rec, 0, len(rows), t)
+        return [int(v) for v in t[:n]]
+
     def poll(self, ticket: int):
         return L.xg_poll(self.ctx, ticket)
 

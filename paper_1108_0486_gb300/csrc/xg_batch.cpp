@@ -11,6 +11,13 @@
 
 namespace xg {
 
+// Threads per block of the persistent batch kernel: one warp, so that a
+// block retires as soon as its warp finds no more work.  With several batch
+// kernels in flight (the server's lanes) a block of four warps would hold
+// the registers of all four until its slowest warp ended.
+constexpr int kBatchBlock = 32;
+constexpr int kWarpsPerBlock = kBatchBlock / 32;
+
 static uint64_t words_of(uint32_t kind, uint64_t count)
 {
     return kind == kNormal ? count + (count & 1u) : count;
@@ -190,7 +197,7 @@ xg_status BatchLauncher::build_graph(xg_ctx* c)
     cudaKernelNodeParams kp{};
     kp.func = const_cast<void*>(batch_kernel_ptr((int)c->param_set));
     kp.gridDim = dim3(1);
-    kp.blockDim = dim3(128);
+    kp.blockDim = dim3(kBatchBlock);
     kp.sharedMemBytes = 0;
     kp.kernelParams = params;
     if (cudaGraphAddKernelNode(&kernel_node_, graph_, &copy_node_, 1, &kp) != cudaSuccess) return XG_ECUDA;
@@ -215,14 +222,15 @@ xg_status BatchLauncher::reserve(xg_ctx* c, uint32_t capacity)
     if (!done_ && cudaEventCreateWithFlags(&done_, cudaEventDisableTiming) != cudaSuccess) return XG_ECUDA;
     capacity_ = cap;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel_ptr((int)c->param_set), 128, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel_ptr((int)c->param_set), kBatchBlock, 0) !=
         cudaSuccess)
         return XG_ECUDA;
     max_grid_ = std::max(1, blocks) * c->sm_count;
     return build_graph(c);
 }
 
-uint64_t BatchLauncher::choose_piece_len(const xg_ctx* c, const HostItem* items, uint32_t n) const
+uint64_t BatchLauncher::choose_piece_len(const xg_ctx* c, const HostItem* items, uint32_t n,
+                                         uint64_t min_piece) const
 {
     if (c->split_words == 1) return 0;  // never cut
     if (c->split_words > 1) return c->split_words;
@@ -234,9 +242,10 @@ uint64_t BatchLauncher::choose_piece_len(const xg_ctx* c, const HostItem* items,
         total += w;
         longest = std::max(longest, w);
     }
-    const uint64_t warps = (uint64_t)std::max(1, max_grid_) * 4;
+    const uint64_t warps = (uint64_t)std::max(1, max_grid_) * kWarpsPerBlock;
     uint64_t per_warp = std::max<uint64_t>(1, total / warps);
-    uint64_t len = uint64_t(1) << 16;
+    uint64_t len = kMinPiece;
+    while (len < min_piece) len *= 2;
     // about two units per resident warp
     while (len * 4 <= per_warp && len < (uint64_t(1) << 22)) len *= 2;
     return longest >= 2 * len ? len : 0;
@@ -356,7 +365,7 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
 }
 
 xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s,
-                                uint32_t* units_per_item)
+                                uint32_t* units_per_item, uint64_t min_piece)
 {
     if (!exec_) {
         if (xg_status st = reserve(c, std::max<uint32_t>(n, 64))) return st;
@@ -364,7 +373,7 @@ xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cu
     if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
     // the jump prologue needs only the pieces: enqueue it before ordering the
     // heads, so that the GPU starts while the host finishes the plan
-    plan_units(items, n, choose_piece_len(c, items, n), c->n, plan_);
+    plan_units(items, n, choose_piece_len(c, items, n, min_piece), c->n, plan_);
     const uint32_t nu = (uint32_t)plan_.units.size();
     if (xg_status st = reserve(c, nu)) return st;
     if (xg_status st = prologue(c, s)) return st;
@@ -384,13 +393,14 @@ xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cu
     if (cudaGraphExecMemcpyNodeSetParams1D(exec_, copy_node_, d_scratch_, h_staging_, used,
                                            cudaMemcpyHostToDevice) != cudaSuccess)
         return XG_ECUDA;
-    const unsigned grid = (unsigned)std::min<uint64_t>(max_grid_, (plan_.heads.size() + 3) / 4);
+    const unsigned grid = (unsigned)std::min<uint64_t>(
+        max_grid_, (plan_.heads.size() + kWarpsPerBlock - 1) / kWarpsPerBlock);
     args_.st = c->st;
     void* params[] = {&args_};
     cudaKernelNodeParams kp{};
     kp.func = const_cast<void*>(batch_kernel_ptr((int)c->param_set));
     kp.gridDim = dim3(std::max(1u, grid));
-    kp.blockDim = dim3(128);
+    kp.blockDim = dim3(kBatchBlock);
     kp.sharedMemBytes = 0;
     kp.kernelParams = params;
     if (cudaGraphExecKernelNodeSetParams(exec_, kernel_node_, &kp) != cudaSuccess) return XG_ECUDA;

@@ -51,8 +51,12 @@ public:
     // stream s.  Waits first for this launcher's previous replay to finish
     // reading its staging buffers.  units_per_item (optional, n entries)
     // receives how many completion increments each item will produce.
+    // min_piece: the shortest piece the automatic choice may cut (a caller
+    // that knows the GPU is already busy raises it: cutting buys latency at
+    // the price of jump-ahead work, about 3.4e4 words' worth per piece).
     xg_status launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s,
-                     uint32_t* units_per_item = nullptr);
+                     uint32_t* units_per_item = nullptr, uint64_t min_piece = kMinPiece);
+    static constexpr uint64_t kMinPiece = uint64_t(1) << 16;
     // Preallocate the jump prologue's buffers for up to `pieces` pieces (so
     // that a later launch does not allocate).
     xg_status reserve_jump(uint32_t pieces, uint32_t pairs);
@@ -64,7 +68,7 @@ private:
     xg_status build_graph(xg_ctx* c);
     xg_status prologue(xg_ctx* c, cudaStream_t s);
     xg_status grow_jump(size_t want);
-    uint64_t choose_piece_len(const xg_ctx* c, const HostItem* items, uint32_t n) const;
+    uint64_t choose_piece_len(const xg_ctx* c, const HostItem* items, uint32_t n, uint64_t min_piece) const;
     uint32_t capacity_ = 0;
     size_t bytes_ = 0;
     void* h_staging_ = nullptr;   // pinned

@@ -17,12 +17,14 @@
 #include <cstdlib>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
 #include <new>
 #include <queue>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
@@ -57,26 +59,27 @@ public:
             return fail(XG_ENOMEM, "server pool: cudaMalloc(%zu) failed", cap_);
         }
         free_.clear();
-        free_[0] = cap_;
+        by_size_.clear();
+        add_free(0, cap_);
         return XG_OK;
     }
+    // Best fit in O(log n): the smallest free block that holds the request.
     void* alloc(size_t bytes)
     {
         bytes = (bytes + kAlign - 1) / kAlign * kAlign;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                const size_t off = it->first, sz = it->second;
-                free_.erase(it);
-                if (sz > bytes) free_[off + bytes] = sz - bytes;
-                used_[off] = bytes;
-                return base_ + off;
-            }
-        }
-        return nullptr;
+        auto it = by_size_.lower_bound(bytes);
+        if (it == by_size_.end()) return nullptr;
+        const size_t sz = it->first, off = it->second;
+        by_size_.erase(it);
+        free_.erase(off);
+        if (sz > bytes) add_free(off + bytes, sz - bytes);
+        used_[off] = bytes;
+        return base_ + off;
     }
+    // Return a block, merging it with free neighbours.
     void release(void* p)
     {
-        const size_t off = static_cast<char*>(p) - base_;
+        size_t off = static_cast<char*>(p) - base_;
         auto u = used_.find(off);
         if (u == used_.end()) return;
         size_t sz = u->second;
@@ -84,16 +87,19 @@ public:
         auto next = free_.lower_bound(off);
         if (next != free_.end() && off + sz == next->first) {
             sz += next->second;
+            drop_size(next->second, next->first);
             next = free_.erase(next);
         }
         if (next != free_.begin()) {
             auto prev = std::prev(next);
             if (prev->first + prev->second == off) {
-                prev->second += sz;
-                return;
+                off = prev->first;
+                sz += prev->second;
+                drop_size(prev->second, prev->first);
+                free_.erase(prev);
             }
         }
-        free_[off] = sz;
+        add_free(off, sz);
     }
     size_t capacity() const { return cap_; }
 
@@ -101,7 +107,22 @@ private:
     static constexpr size_t kAlign = 256;
     char* base_ = nullptr;
     size_t cap_ = 0;
-    std::map<size_t, size_t> free_;
+    void add_free(size_t off, size_t sz)
+    {
+        free_[off] = sz;
+        by_size_.emplace(sz, off);
+    }
+    void drop_size(size_t sz, size_t off)
+    {
+        auto r = by_size_.equal_range(sz);
+        for (auto it = r.first; it != r.second; ++it)
+            if (it->second == off) {
+                by_size_.erase(it);
+                return;
+            }
+    }
+    std::map<size_t, size_t> free_;            // offset -> size
+    std::multimap<size_t, size_t> by_size_;    // size -> offset
     std::unordered_map<size_t, size_t> used_;
 };
 
@@ -158,6 +179,13 @@ public:
         // host-side fault injection for tests: the first N batch launches
         // report failure without reaching the GPU
         if (const char* f = std::getenv("XG_INJECT_LAUNCH_FAILURES")) inject_failures_ = std::atoi(f);
+        // optional per-batch trace, written as CSV when the server stops
+        if (const char* f = std::getenv("XG_SERVER_TRACE")) {
+            trace_path_ = f;
+            for (auto& l : lanes_)
+                if (cudaEventCreate(&l.ev0) != cudaSuccess || cudaEventCreate(&l.ev1) != cudaSuccess)
+                    return fail(XG_ECUDA, "server: trace event creation failed");
+        }
         run_ = true;
         th_ = std::thread([this] { loop(); });
         return XG_OK;
@@ -176,8 +204,12 @@ public:
                 cudaStreamDestroy(l.stream);
                 l.stream = nullptr;
             }
+            if (l.ev0) cudaEventDestroy(l.ev0);
+            if (l.ev1) cudaEventDestroy(l.ev1);
+            l.ev0 = l.ev1 = nullptr;
         }
         lanes_.clear();
+        write_trace();
         if (h_flags_) cudaFreeHost(h_flags_);
         h_flags_ = nullptr;
     }
@@ -192,7 +224,7 @@ public:
         auto t = std::make_shared<Ticket>();
         t->req = r;
         t->bytes = (size_t)r.count * 4;
-        std::lock_guard<std::mutex> lk(mu_);
+        std::lock_guard<std::mutex> lk(adm_mu_);
         if (outstanding_ + t->bytes > cfg_.mem_cap_bytes) {
             ++refused_;
             return fail(XG_EAGAIN, "admission refused: %zu bytes outstanding, cap %llu", outstanding_,
@@ -213,16 +245,79 @@ public:
         t->seq = t->id;
         t->t_submit = now_ns();
         tickets_[t->id] = t;
-        incoming_.push_back(t);
         ++submitted_;
         *ticket = t->id;
+        {
+            // nested (admission, then queue): per stream, queue order is ticket order
+            std::lock_guard<std::mutex> ql(mu_);
+            incoming_.push_back(t);
+        }
         cv_.notify_one();
+        return XG_OK;
+    }
+
+    // Admit reqs[0..n) in order under one lock, stopping at the first one the
+    // cap or the pool refuses.  All are validated first: an invalid request
+    // admits none.
+    xg_status submit_many(const xg_request* reqs, uint32_t n, uint64_t* tickets, uint32_t* n_accepted)
+    {
+        *n_accepted = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            const xg_request& r = reqs[i];
+            if (r.stream >= c_->n) return fail(XG_EINVAL, "request %u: stream %u out of range", i, r.stream);
+            if (r.type > XG_NORMAL_F32) return fail(XG_EINVAL, "request %u: unknown type %u", i, r.type);
+            if (r.count == 0) return fail(XG_EINVAL, "request %u: empty request", i);
+            if (reinterpret_cast<uintptr_t>(r.d_out) & 3u)
+                return fail(XG_EINVAL, "request %u: output not 4-byte aligned", i);
+        }
+        std::vector<std::shared_ptr<Ticket>> made;
+        made.reserve(n);
+        std::lock_guard<std::mutex> lk(adm_mu_);
+        const uint64_t now = now_ns();
+        uint32_t k = 0;
+        for (; k < n; ++k) {
+            // tickets only for the requests admitted (a refused tail makes none)
+            const size_t bytes = (size_t)reqs[k].count * 4;
+            if (outstanding_ + bytes > cfg_.mem_cap_bytes) break;
+            void* out = reqs[k].d_out;
+            const bool pooled = out == nullptr;
+            if (pooled) {
+                out = pool_.alloc(bytes);
+                if (!out) break;
+            }
+            made.push_back(std::make_shared<Ticket>());
+            auto& t = made.back();
+            t->req = reqs[k];
+            t->bytes = bytes;
+            t->out = out;
+            t->pooled = pooled;
+            outstanding_ += t->bytes;
+            t->id = next_id_++;
+            t->seq = t->id;
+            t->t_submit = now;
+            tickets_[t->id] = t;
+            tickets[k] = t->id;
+        }
+        submitted_ += k;
+        *n_accepted = k;
+        if (k) {
+            {
+                std::lock_guard<std::mutex> ql(mu_);
+                incoming_.insert(incoming_.end(), made.begin(), made.begin() + k);
+            }
+            cv_.notify_one();
+        }
+        if (k < n) {
+            ++refused_;
+            return fail(XG_EAGAIN, "admission refused at request %u: %zu bytes outstanding, cap %llu", k,
+                        outstanding_, (unsigned long long)cfg_.mem_cap_bytes);
+        }
         return XG_OK;
     }
 
     std::shared_ptr<Ticket> find(uint64_t id)
     {
-        std::lock_guard<std::mutex> lk(mu_);
+        std::lock_guard<std::mutex> lk(adm_mu_);
         auto it = tickets_.find(id);
         return it == tickets_.end() ? nullptr : it->second;
     }
@@ -269,7 +364,7 @@ public:
 
     xg_status release(uint64_t id)
     {
-        std::lock_guard<std::mutex> lk(mu_);
+        std::lock_guard<std::mutex> lk(adm_mu_);
         auto it = tickets_.find(id);
         if (it == tickets_.end()) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
         Ticket& t = *it->second;
@@ -301,15 +396,17 @@ public:
     xg_status collect(xg_completion* out, uint32_t max, uint32_t* n_out, int release)
     {
         uint32_t n = 0;
-        std::lock_guard<std::mutex> lk(mu_);
-        while (n < max) {
-            std::shared_ptr<Ticket> t;
-            {
-                std::lock_guard<std::mutex> dl(done_mu_);
-                if (done_q_.empty()) break;
-                t = done_q_.front();
-                done_q_.pop_front();
-            }
+        std::vector<std::shared_ptr<Ticket>> got;
+        {
+            // take up to max finished tickets in one go
+            std::lock_guard<std::mutex> dl(done_mu_);
+            const size_t k = std::min<size_t>(max, done_q_.size());
+            got.assign(std::make_move_iterator(done_q_.begin()), std::make_move_iterator(done_q_.begin() + k));
+            done_q_.erase(done_q_.begin(), done_q_.begin() + k);
+        }
+        std::vector<std::shared_ptr<Ticket>> dropped;   // freed after the lock is released
+        std::lock_guard<std::mutex> lk(adm_mu_);
+        for (auto& t : got) {
             auto it = tickets_.find(t->id);
             if (it == tickets_.end()) continue;  // already released by its owner
             xg_completion& c = out[n++];
@@ -323,17 +420,18 @@ public:
             if (release) {
                 if (t->pooled) pool_.release(t->out);
                 outstanding_ -= t->bytes;
+                dropped.push_back(std::move(it->second));
                 tickets_.erase(it);
                 c.d_result = nullptr;
             }
         }
         *n_out = n;
-        return XG_OK;
+        return XG_OK;   // lk unlocks before dropped (declared earlier) frees the tickets
     }
 
     void stats(xg_server_stats* s)
     {
-        std::lock_guard<std::mutex> lk(mu_);
+        std::lock_guard<std::mutex> lk(adm_mu_);
         s->submitted = submitted_;
         s->completed = completed_.load();
         s->refused = refused_;
@@ -352,23 +450,51 @@ private:
         std::unique_ptr<BatchLauncher> launcher;
         std::vector<std::shared_ptr<Ticket>> inflight;
         bool busy = false;
+        uint64_t words = 0;  // words of the batch in flight
+        // tracing (XG_SERVER_TRACE): GPU start/end of the batch in flight
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        uint64_t t_launch = 0, t_host = 0;
+        uint32_t n_items = 0, n_units = 0;
     };
+    struct TraceRec {
+        uint32_t lane, items, units;
+        uint64_t words, t_launch_ns, host_ns, t_seen_done_ns;
+        float gpu_ms;
+    };
+
+    // Shortest piece a new batch may cut its calls into, from the words the
+    // GPU already has in flight: cutting shortens one call's critical path
+    // but costs jump-ahead work (about 3.4e4 words' worth per piece), which
+    // only pays while the GPU would otherwise idle.  B is about 1.5 ms of
+    // work: 2^18 words for each of 32 warps per SM.
+    uint64_t min_piece_for_backlog() const
+    {
+        const uint64_t B = (uint64_t)c_->sm_count * 32 * (uint64_t(1) << 18);
+        if (inflight_words_ < B / 8) return BatchLauncher::kMinPiece;
+        if (inflight_words_ < B) return uint64_t(1) << 18;
+        return uint64_t(1) << 21;
+    }
 
     void loop()
     {
         std::vector<std::shared_ptr<Ticket>> fresh;
         std::vector<HostItem> items;
         std::vector<uint32_t> units;
+        const bool timed = !trace_path_.empty();
         while (run_.load()) {
             bool progress = false;
+            const uint64_t q0 = timed ? now_ns() : 0;
             {
                 std::unique_lock<std::mutex> lk(mu_);
+                if (timed) loop_ns_[0] += now_ns() - q0;   // waiting for the lock
                 if (incoming_.empty() && !any_busy() && ready_.empty()) {
                     cv_.wait_for(lk, std::chrono::milliseconds(2));
                 }
                 fresh.assign(incoming_.begin(), incoming_.end());
                 incoming_.clear();
             }
+            const uint64_t q1 = timed ? now_ns() : 0;
+            ++loop_iters_;
             for (auto& t : fresh) {
                 auto& q = fifo_[t->req.stream];
                 q.push_back(t);
@@ -377,19 +503,21 @@ private:
                 progress = true;
             }
             fresh.clear();
+            const uint64_t q2 = timed ? now_ns() : 0;
             // completions
             for (size_t li = 0; li < lanes_.size(); ++li) {
                 Lane& l = lanes_[li];
                 if (!l.busy) continue;
-                bool all = true;
-                for (auto& t : l.inflight) {
-                    if (!t) continue;
-                    if (check_flag(*t)) {
-                        finish(t);
-                        t.reset();
+                // finished tickets leave the lane's list (swap with the last),
+                // so later scans visit only the ones still running
+                for (size_t k = 0; k < l.inflight.size();) {
+                    if (check_flag(*l.inflight[k])) {
+                        finish(l.inflight[k]);
+                        l.inflight[k] = std::move(l.inflight.back());
+                        l.inflight.pop_back();
                         progress = true;
                     } else {
-                        all = false;
+                        ++k;
                     }
                 }
                 cudaError_t e = cudaEventQuery(l.launcher->done_event());
@@ -398,25 +526,38 @@ private:
                     // finished if its flag has become visible meanwhile,
                     // failed (not run: launch or kernel error) otherwise
                     for (auto& t : l.inflight) {
-                        if (!t) continue;
                         if (check_flag(*t)) finish(t);
                         else fail_ticket(t);
                     }
                     if (e != cudaSuccess) cudaGetLastError();
+                    if (l.ev0) {
+                        float ms = -1.f;
+                        if (cudaEventElapsedTime(&ms, l.ev0, l.ev1) != cudaSuccess) {
+                            cudaGetLastError();
+                            ms = -1.f;
+                        }
+                        trace_.push_back(TraceRec{(uint32_t)li, l.n_items, l.n_units, l.words, l.t_launch, l.t_host,
+                                                  now_ns(), ms});
+                    }
                     l.busy = false;
                     l.inflight.clear();
+                    l.words = 0;
                     progress = true;
                 }
-                (void)all;
             }
-            // launches
-            for (size_t li = 0; li < lanes_.size() && !ready_.empty(); ++li) {
+            const uint64_t q3 = timed ? now_ns() : 0;
+            // launches.  While the GPU already has about 1.5 ms of work in
+            // flight, new requests wait and gather into larger batches (an
+            // earlier launch would only queue behind that work).
+            const uint64_t busy_words = (uint64_t)c_->sm_count * 32 * (uint64_t(1) << 18);
+            for (size_t li = 0; li < lanes_.size() && !ready_.empty() && inflight_words_ < busy_words; ++li) {
                 Lane& l = lanes_[li];
                 if (l.busy) continue;
                 items.clear();
                 l.inflight.clear();
                 std::memset(h_flags_ + li * cfg_.max_batch, 0, (size_t)cfg_.max_batch * 4);
                 const uint64_t t_launch = now_ns();
+                uint64_t batch_words = 0;
                 while (!ready_.empty() && items.size() < cfg_.max_batch) {
                     const uint32_t s = ready_.top().second;
                     ready_.pop();
@@ -428,18 +569,30 @@ private:
                     t->slot = (uint32_t)(li * cfg_.max_batch + items.size());
                     t->t_launch = t_launch;
                     items.push_back(HostItem{s, t->req.type, t->req.count, t->out, d_flags_ + t->slot});
+                    batch_words += t->req.count;
                     l.inflight.push_back(t);
                     --queued_;
                 }
                 if (items.empty()) continue;
                 in_flight_ += items.size();
+                const uint64_t min_piece = min_piece_for_backlog();
+                inflight_words_ += batch_words;   // finish() takes each request's share back
                 units.resize(items.size());
                 xg_status lst = XG_ECUDA;
                 if (inject_failures_ > 0) --inject_failures_;
                 else {
                     const uint64_t h0 = now_ns();
-                    lst = l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream, units.data());
-                    launch_ns_ += now_ns() - h0;
+                    if (l.ev0) cudaEventRecord(l.ev0, l.stream);
+                    lst = l.launcher->launch(c_, items.data(), (uint32_t)items.size(), l.stream, units.data(),
+                                             min_piece);
+                    if (l.ev1) cudaEventRecord(l.ev1, l.stream);
+                    const uint64_t h1 = now_ns();
+                    launch_ns_ += h1 - h0;
+                    l.t_launch = h0;
+                    l.t_host = h1 - h0;
+                    l.n_items = (uint32_t)items.size();
+                    l.n_units = 0;
+                    for (uint32_t u : units) l.n_units += u;
                 }
                 for (size_t j = 0; j < l.inflight.size(); ++j) {
                     l.inflight[j]->expected = lst == XG_OK ? units[j] : 1u;
@@ -453,12 +606,39 @@ private:
                     continue;
                 }
                 l.busy = true;
+                l.words = batch_words;
                 ++batches_;
                 items_launched_ += items.size();
                 progress = true;
             }
+            if (timed) {
+                const uint64_t q4 = now_ns();
+                loop_ns_[1] += q2 - q1;   // queueing new requests
+                loop_ns_[2] += q3 - q2;   // completion scan
+                loop_ns_[3] += q4 - q3;   // launches
+            }
             if (!progress) std::this_thread::yield();
         }
+    }
+
+    void write_trace()
+    {
+        if (trace_path_.empty()) return;
+        if (FILE* f = std::fopen(trace_path_.c_str(), "w")) {
+            std::fprintf(f, "lane,items,units,words,t_launch_ns,host_ns,t_seen_done_ns,gpu_ms\n");
+            std::fprintf(f, "# loop iterations %llu; ns waiting for the lock %llu, queueing %llu, "
+                            "completion scan %llu, launches %llu\n",
+                         (unsigned long long)loop_iters_, (unsigned long long)loop_ns_[0],
+                         (unsigned long long)loop_ns_[1], (unsigned long long)loop_ns_[2],
+                         (unsigned long long)loop_ns_[3]);
+            for (const TraceRec& r : trace_)
+                std::fprintf(f, "%u,%u,%u,%llu,%llu,%llu,%llu,%.4f\n", r.lane, r.items, r.units,
+                             (unsigned long long)r.words, (unsigned long long)r.t_launch_ns,
+                             (unsigned long long)r.host_ns, (unsigned long long)r.t_seen_done_ns, r.gpu_ms);
+            std::fclose(f);
+        }
+        trace_.clear();
+        trace_path_.clear();  // stop() may run again (destructor): write once
     }
 
     bool any_busy() const
@@ -478,6 +658,7 @@ private:
     void finish(const std::shared_ptr<Ticket>& t)
     {
         const uint32_t s = t->req.stream;
+        inflight_words_ -= t->req.count;
         busy_streams_.erase(s);
         auto it = fifo_.find(s);
         if (it != fifo_.end() && !it->second.empty()) ready_.push({it->second.front()->seq, s});
@@ -490,7 +671,8 @@ private:
     xg_ctx* c_;
     xg_server_config cfg_{};
     DevicePool pool_;
-    std::mutex mu_;
+    std::mutex adm_mu_;  // admission: outstanding_, pool_, tickets_, counters (taken before mu_)
+    std::mutex mu_;      // incoming_ and cv_
     std::condition_variable cv_;
     std::unordered_map<uint64_t, std::shared_ptr<Ticket>> tickets_;
     std::deque<std::shared_ptr<Ticket>> incoming_;
@@ -503,6 +685,10 @@ private:
     int inject_failures_ = 0;
     std::mutex done_mu_;
     std::deque<std::shared_ptr<Ticket>> done_q_;  // finished, not yet collected
+    uint64_t inflight_words_ = 0;                 // scheduler thread only
+    std::string trace_path_;
+    uint64_t loop_iters_ = 0, loop_ns_[4] = {0, 0, 0, 0};  // scheduler thread only
+    std::vector<TraceRec> trace_;                 // scheduler thread until stop
     // scheduler thread only
     std::unordered_map<uint32_t, std::deque<std::shared_ptr<Ticket>>> fifo_;
     std::unordered_set<uint32_t> busy_streams_;
@@ -563,6 +749,15 @@ xg_status xg_submit(xg_ctx* ctx, const xg_request* req, uint64_t* ticket)
     if (!ctx || !req) return fail(XG_EINVAL, "null argument");
     if (!ctx->server) return fail(XG_EINVAL, "server not running (xg_server_start)");
     return ctx->server->submit(*req, ticket);
+}
+
+xg_status xg_submit_many(xg_ctx* ctx, const xg_request* reqs, uint32_t n, uint64_t* tickets, uint32_t* n_accepted)
+{
+    if (!ctx || !n_accepted || (n && (!reqs || !tickets))) return fail(XG_EINVAL, "null argument");
+    *n_accepted = 0;
+    if (!ctx->server) return fail(XG_EINVAL, "server not running (xg_server_start)");
+    if (n == 0) return XG_OK;
+    return ctx->server->submit_many(reqs, n, tickets, n_accepted);
 }
 
 xg_status xg_poll(xg_ctx* ctx, uint64_t ticket, int* done, void** d_result)

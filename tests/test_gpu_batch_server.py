@@ -399,3 +399,54 @@ def test_server_serving_workload_sampled():
         before = sum(nwords(KINDS[q.kind], q.count) for q in reqs[:i] if q.stream == r.stream)
         words = O.Xorgens.param_set(0).seed(int(seeds[r.stream])).u32(before + nwords(k, r.count))
         check(k, got[i][:r.count], oracle_call(words[before:], k, r.count))
+
+
+def test_submit_many_admits_in_order_and_matches_the_oracle():
+    seeds = W.seeds(50, start=5)
+    reqs = [(i % 50, KINDS[i % 3], 500 + 91 * i) for i in range(120)]
+    with Streams(50, seeds=seeds) as st:
+        srv = st.serve()
+        tickets = srv.submit_many(reqs)
+        assert len(tickets) == len(reqs) and tickets == sorted(tickets)
+        outs = [srv.result(t, k, n).clone() for t, (_, k, n) in zip(tickets, reqs)]
+        for t in tickets:
+            srv.release(t)
+        srv.stop()
+    for (s, k, n), o, ref in zip(reqs, outs, oracle_per_item(seeds, reqs)):
+        check(k, o[:n], ref)
+
+
+def test_submit_many_partial_admission_and_invalid_requests():
+    from paper_1108_0486_gb300 import _lib as L
+    with Streams(4, seeds=[1, 2, 3, 4]) as st:
+        srv = st.serve(mem_cap_bytes=1 << 20)
+        # 400 KB each: the third would pass the 1 MiB cap
+        t = srv.submit_many([(0, "u32", 100000), (1, "u32", 100000), (2, "u32", 100000)])
+        assert len(t) == 2
+        with pytest.raises(L.XGError):     # stream 9 does not exist: nothing admitted
+            srv.submit_many([(3, "u32", 10), (9, "u32", 10)])
+        assert srv.stats()["submitted"] == 2
+        for x in t:
+            srv.wait(x, 60000)
+            srv.release(x)
+        assert len(srv.submit_many([(2, "u32", 100000), (3, "u32", 10)])) == 2
+        srv.stop()
+
+
+def test_server_trace_records_every_batch(tmp_path, monkeypatch):
+    path = tmp_path / "trace.csv"
+    monkeypatch.setenv("XG_SERVER_TRACE", str(path))
+    with Streams(8, seeds=W.seeds(8)) as st:
+        srv = st.serve(lanes=2)
+        tickets = [srv.submit(i % 8, KINDS[i % 3], 5000 + i) for i in range(24)]
+        for t in tickets:
+            srv.wait(t, 60000)
+            srv.release(t)
+        batches = srv.stats()["batches"]
+        srv.stop()
+    lines = path.read_text().splitlines()
+    assert lines[0].startswith("lane,items,units,words")
+    assert lines[1].startswith("# loop iterations")
+    rows = [l.split(",") for l in lines[2:]]
+    assert len(rows) == batches and sum(int(r[1]) for r in rows) == 24
+    assert all(float(r[7]) >= 0 for r in rows)
