@@ -532,7 +532,9 @@ private:
                     if (e != cudaSuccess) cudaGetLastError();
                     if (l.ev0) {
                         float ms = -1.f;
-                        if (cudaEventElapsedTime(&ms, l.ev0, l.ev1) != cudaSuccess) {
+                        // ev1 follows the batch's own completion event: done at most a moment later
+                        if (cudaEventSynchronize(l.ev1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, l.ev0, l.ev1) != cudaSuccess) {
                             cudaGetLastError();
                             ms = -1.f;
                         }
