@@ -11,8 +11,8 @@
  *   XG_PARAMS_DEFAULT  (r,s,a,b,c,d) = (128, 95, 17, 12, 13, 15)
  *   XG_PARAMS_PAPER    (r,s,a,b,c,d) = (128, 65, 15, 14, 12, 17)  (Sec. 2)
  * Each stream is one generator: r state words plus a Weyl word plus a
- * position (Sec. 2: "a small constant for the Weyl generator and a circular
- * array index").  Many independent streams live in one context, resident in
+ * position (Sec. 2 counts the state the same way: the r words, the Weyl
+ * word and the buffer index).  Many independent streams live in one context, resident in
  * device memory (Sec. 2, independent subsequences; Sec. 4, one seed per
  * block id).
  *

@@ -60,7 +60,7 @@ typedef struct {
     uint32_t x[XGO_RMAX];         /* the circular buffer of r words */
 } xgo_gen;
 
-/* Sec. 1.5: "a recommended choice is an odd integer close to 2^{w-1}(sqrt(5)-1)".
+/* Sec. 1.5 recommends for omega an odd integer near 2^(w-1) (sqrt(5) - 1).
  * Reading: the odd integer nearest to that real number. */
 uint32_t xgo_omega(uint32_t w)
 {
