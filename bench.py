@@ -370,6 +370,12 @@ def extra_rows(st, stream, torch, peak):
     ms = _time(lambda: st.u32(n, out=buf.view(torch.int32)), stream, torch)
     rows["u32"] = {"rn_s": rn / (ms / 1e3), "ms": ms, "hbm_frac": rn * 4 / (ms / 1e3) / 1e9 / peak}
     del buf
+    # jump-ahead of every stream: J = 2^40 + 2^20 + 12345 words, 8 set bits,
+    # i.e. 8 applications of a 4096 x 4096 GF(2) matrix per stream
+    J = (1 << 40) + (1 << 20) + 12345
+    ms = _time(lambda: st.jump(J), stream, torch)
+    rows["jump_16384_streams"] = {"words": J, "set_bits": bin(J).count("1"), "ms": ms,
+                                  "us_per_stream_application": ms * 1e3 / (STREAMS * bin(J).count("1"))}
     # one stream, 2^20 words (seed 0x12345678): latency of a single long call
     from paper_1108_0486_gb300 import Streams
     one = Streams(1, seeds=[W.SINGLE_STREAM["seed"]], stream=stream)

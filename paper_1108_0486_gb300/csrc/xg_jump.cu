@@ -349,22 +349,34 @@ extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uin
     xg_status st = XG_OK;
     for (int k = 0; k <= top; ++k)
         if (((words >> k) & 1) && !jump_matrix(ctx->device, (int)ctx->param_set, k, s, &st)) return st;
+    // rings[0, n) hold the states, rings[n, 2n) receive each application
+    // (four-Russians table kernel, as in the batch prologue); the two halves
+    // swap roles after every set bit of words.
     uint32_t* rings = nullptr;
-    uint32_t* ids = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)nstreams * kR * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)nstreams * 4, s);
+    uint32_t* ids = nullptr;   // [0, 2n): stream ids for the gather, then 0..2n-1
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)2 * nstreams * kR * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)3 * nstreams * 4, s);
     if (e != cudaSuccess) return cuda_fail(e, "xg_jump scratch");
-    std::vector<uint32_t> h(nstreams);
+    std::vector<uint32_t> h((size_t)3 * nstreams);
     for (uint32_t i = 0; i < nstreams; ++i) h[i] = first + i;
-    e = cudaMemcpyAsync(ids, h.data(), (size_t)nstreams * 4, cudaMemcpyHostToDevice, s);
+    for (uint32_t i = 0; i < 2 * nstreams; ++i) h[nstreams + i] = i;
+    const uint32_t* lo_idx = ids + nstreams;            // 0 .. n-1
+    const uint32_t* hi_idx = ids + 2 * (size_t)nstreams;  // n .. 2n-1
+    e = cudaMemcpyAsync(ids, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_gather_rings(ctx->st, ids, nstreams, rings, nullptr, nullptr, 0, 0, s);
+    bool in_lo = true;
     for (int k = 0; k <= top && e == cudaSuccess; ++k) {
         if (!((words >> k) & 1)) continue;
         const uint64_t* C = jump_matrix(ctx->device, (int)ctx->param_set, k, s, &st);
-        e = launch_gf2_apply(C, reinterpret_cast<uint64_t*>(rings), nstreams, nullptr, s);
+        const uint32_t* src = in_lo ? lo_idx : hi_idx;
+        const uint32_t* dst = in_lo ? hi_idx : lo_idx;
+        e = zero_rings(rings, dst, nstreams, s);
+        if (e == cudaSuccess) e = launch_gf2_apply_pairs(C, rings, nstreams, src, dst, ctx->sm_count, s);
+        in_lo = !in_lo;
     }
     if (e == cudaSuccess) {
-        scatter_rings_kernel<<<nstreams, 128, 0, s>>>(ctx->st, first, nstreams, rings, words,
+        const uint32_t* res = in_lo ? rings : rings + (size_t)nstreams * kR;
+        scatter_rings_kernel<<<nstreams, 128, 0, s>>>(ctx->st, first, nstreams, res, words,
                                                       ctx->weyl_on ? 0x9E3779B9u : 0u);
         e = cudaGetLastError();
     }
