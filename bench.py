@@ -437,6 +437,15 @@ def batched_row(torch, L, stream, peak, reps=3):
         st.set_batch_split(1 << q)
         by_piece[f"2^{q}"] = _time(lambda: L.xg_generate_batch(st.ctx, arr), stream, torch, reps=reps, warm=2)
     st.set_batch_split(0)
+    # the same lengths with a single output type: the batch machinery
+    # against the HBM floor when no normal transform limits it
+    by_type = {}
+    for k, name in ((0, "u32"), (1, "uniform"), (2, "normal")):
+        arr_k = L.make_items([(s_, k, c_, p_) for s_, _, c_, p_ in spec])
+        ms_k = _time(lambda: L.xg_generate_batch(st.ctx, arr_k), stream, torch, reps=reps, warm=2)
+        words_k = sum(it.count + (it.count & 1 if k == 2 else 0) for it in items)
+        by_type[name] = {"ms": ms_k, "rn_s": total / (ms_k / 1e3),
+                         "hbm_frac": total * 4 / (ms_k / 1e3) / 1e9 / peak, "words": words_k}
     longest = max(range(len(items)), key=lambda i: items[i].count)
     one = L.make_items([spec[longest]])
     ms_long = _time(lambda: L.xg_generate_batch(st.ctx, one), stream, torch, reps=reps, warm=2)
@@ -446,7 +455,7 @@ def batched_row(torch, L, stream, peak, reps=3):
     return {"workload": "4096 items (streams 0..4095, seeds 1..4096), lengths log-uniform [2^10, 2^24] "
                         "(PCG64 seed 1108), types uniform over u32/uniform/normal, one graph-replayed launch",
             "rns_total": total, "ms": ms, "rn_s": total / (ms / 1e3), "host_call_ms": min(host),
-            "ms_by_forced_piece_len": by_piece,
+            "ms_by_forced_piece_len": by_piece, "same_lengths_one_type": by_type,
             "hbm_frac": total * 4 / (ms / 1e3) / 1e9 / peak,
             "longest_item": items[longest].count, "longest_item_alone_ms": ms_long,
             "hbm_floor_ms": total * 4 / peak / 1e6}
