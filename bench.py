@@ -289,6 +289,8 @@ def run_ours(args):
         step(record=True)
     t_end.record(stream)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     ms = t_start.elapsed_time(t_end)
     clk = clocks.stop()
     ms = max_over_ranks(ms, dist, "cuda")
@@ -309,7 +311,8 @@ def run_ours(args):
                 "per_kernel_ms": {"u32": avg_u, "uniform": avg_f}}
 
     rows = {}
-    if not args.quick:
+    if not args.quick and rank == 0:
+        # the other rows run on one GPU (with N > 1 the other ranks wait)
         rows = extra_rows(st, stream, torch, peak)
         rows["batched"] = batched_row(torch, L, stream, peak)
         rows["serving"] = serving_row(torch, L, stream, seconds=args.serve_seconds)
@@ -318,9 +321,11 @@ def run_ours(args):
             rows["curand_xorwow_context"] = curand_row(torch, stream)
         except Exception as e:  # context only: never fail the bench on it
             rows["curand_xorwow_context"] = {"unavailable": str(e)[:200]}
+    if dist:
+        dist.barrier()
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(st, stream, torch, L, args)
+        e2e = end_to_end(st, stream, torch, L, args, dist, ws)
     torch.cuda.synchronize()
     st.close()
     del buf_u, buf_f
@@ -329,7 +334,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": dict(CONFIG, parallelism=f"independent streams x{ws}", launch=tuned),
-                "roofline": roofline, "gpu_launches": launches_per_step * args.steps,
+                "roofline": roofline, "gpu_launches": launches_per_step * args.steps * ws,
                 "clocks": clk, "e2e": e2e, "rows": rows}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
@@ -681,10 +686,11 @@ def curand_row(torch, stream, n=1 << 30):
             "normal_rn_s": n / (ms_n / 1e3), "u32_ms": ms_u, "normal_ms": ms_n}
 
 
-def end_to_end(st, stream, torch, L, args):
+def end_to_end(st, stream, torch, L, args, dist=None, ws=1):
     """The same step through the C ABI into pinned host memory: each call
     generates on the device in pieces and copies them to the host while the
-    next piece is generated; the timed region includes every copy."""
+    next piece is generated; the timed region includes every copy.  With
+    N ranks the job's time is the slowest rank's and the bytes are the job's."""
     host = torch.empty((STREAMS, N_PER), dtype=torch.int32, pin_memory=True)
     hostf = torch.empty((STREAMS, N_PER), dtype=torch.float32, pin_memory=True)
     ptr_u, ptr_f = host.data_ptr(), hostf.data_ptr()
@@ -696,14 +702,17 @@ def end_to_end(st, stream, torch, L, args):
     step()
     torch.cuda.synchronize()
     k = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(k):
         step()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    rns = STREAMS * N_PER * 2 * k / dt
+    dt = max_over_ranks(dt * 1e3, dist, "cuda") / 1e3
+    rns = STREAMS * N_PER * 2 * k * ws / dt
     return {"value": rns, "unit": UNIT, "h2d_bytes_per_step": 0,
-            "d2h_bytes_per_step": STREAMS * N_PER * 8, "steps": k,
+            "d2h_bytes_per_step": STREAMS * N_PER * 8 * ws, "steps": k,
             "note": "host buffers are pinned; no inputs cross per step (state resident)"}
 
 

@@ -103,6 +103,21 @@ xg_status xg_get_state(xg_ctx* ctx, uint32_t stream, uint32_t* host_ring128,
 xg_status xg_set_state(xg_ctx* ctx, uint32_t stream, const uint32_t* host_ring128,
                        uint32_t weyl);
 
+/* Bulk checkpoint of streams [first, first + count): host_rings receives
+ * count x 128 words (stream after stream, each oldest first, as
+ * xg_get_state), host_weyl count Weyl words, host_pos (may be NULL) count
+ * positions (words consumed since seeding).  Synchronous; about 0.5 KiB per
+ * stream through one kernel and three copies. */
+xg_status xg_get_states(xg_ctx* ctx, uint32_t first, uint32_t count, uint32_t* host_rings,
+                        uint32_t* host_weyl, uint64_t* host_pos);
+
+/* Bulk restore of states written by xg_get_states (into this or another
+ * context with the same parameter set): the streams continue exactly as the
+ * checkpointed ones did.  Positions are restored when host_pos is not NULL,
+ * else left as they are.  Synchronous. */
+xg_status xg_set_states(xg_ctx* ctx, uint32_t first, uint32_t count, const uint32_t* host_rings,
+                        const uint32_t* host_weyl, const uint64_t* host_pos);
+
 /* ---- plain generation (one kernel launch per call) --------------------- */
 
 /* Write n_per_stream outputs of each stream in [first, first+nstreams) to

@@ -68,6 +68,8 @@ SIGNATURES = {
     "xg_seed": [vp, u32, u32, vp],
     "xg_get_state": [vp, u32, vp, P_u32],
     "xg_set_state": [vp, u32, vp, u32],
+    "xg_get_states": [vp, u32, u32, vp, vp, vp],
+    "xg_set_states": [vp, u32, u32, vp, vp, vp],
     "xg_generate_u32": [vp, u32, u32, u64, vp, u64],
     "xg_generate_uniform": [vp, u32, u32, u64, vp, u64],
     "xg_generate_normal": [vp, u32, u32, u64, vp, u64],
@@ -176,6 +178,16 @@ def xg_get_state(ctx: int, stream: int, host_ring_ptr: int) -> int:
 
 def xg_set_state(ctx: int, stream: int, host_ring_ptr: int, weyl: int) -> None:
     call("xg_set_state", ctypes.c_void_p(ctx), stream, ctypes.c_void_p(host_ring_ptr), weyl & 0xFFFFFFFF)
+
+
+def xg_get_states(ctx, first, count, rings_ptr, weyl_ptr, pos_ptr=0) -> None:
+    call("xg_get_states", ctypes.c_void_p(ctx), first, count, ctypes.c_void_p(rings_ptr),
+         ctypes.c_void_p(weyl_ptr), ctypes.c_void_p(pos_ptr or None))
+
+
+def xg_set_states(ctx, first, count, rings_ptr, weyl_ptr, pos_ptr=0) -> None:
+    call("xg_set_states", ctypes.c_void_p(ctx), first, count, ctypes.c_void_p(rings_ptr),
+         ctypes.c_void_p(weyl_ptr), ctypes.c_void_p(pos_ptr or None))
 
 
 def xg_generate_u32(ctx, first, nstreams, n_per_stream, out_ptr, ld) -> None:

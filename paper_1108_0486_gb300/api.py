@@ -72,6 +72,26 @@ class Streams:
         assert r.size == 128
         L.xg_set_state(self.ctx, stream, r.ctypes.data, weyl)
 
+    def checkpoint(self, first: int = 0, count=None) -> dict:
+        """Every stream's state in [first, first + count) as host arrays:
+        rings (count, 128) uint32, weyl (count,) uint32, pos (count,) uint64."""
+        count = self.n - first if count is None else count
+        rings = np.zeros((count, 128), dtype=np.uint32)
+        weyl = np.zeros(count, dtype=np.uint32)
+        pos = np.zeros(count, dtype=np.uint64)
+        L.xg_get_states(self.ctx, first, count, rings.ctypes.data, weyl.ctypes.data, pos.ctypes.data)
+        return {"first": first, "rings": rings, "weyl": weyl, "pos": pos}
+
+    def restore(self, ckpt: dict, first=None, positions: bool = True):
+        """Load a checkpoint (from this or another context of the same
+        parameter set) into streams [first, first + count)."""
+        first = ckpt["first"] if first is None else first
+        rings = np.ascontiguousarray(ckpt["rings"], dtype=np.uint32)
+        weyl = np.ascontiguousarray(ckpt["weyl"], dtype=np.uint32)
+        pos = np.ascontiguousarray(ckpt["pos"], dtype=np.uint64)
+        L.xg_set_states(self.ctx, first, weyl.size, rings.ctypes.data, weyl.ctypes.data,
+                        pos.ctypes.data if positions else 0)
+
     def set_launch(self, kind: str, tpg: int = 0, wpl: int = 0):
         L.xg_set_launch(self.ctx, TYPES[kind], tpg, wpl)
 

@@ -113,6 +113,11 @@ cudaError_t launch_transform(int out_kind, const uint32_t* in, uint64_t n, float
                              cudaStream_t s);
 
 cudaError_t launch_batch(int param_set, const BatchArgs& a, unsigned grid, cudaStream_t s);
+// Bulk checkpoint and restore of streams [first, first + n) (128-word rings).
+cudaError_t launch_export_states(const State& st, uint32_t first, uint32_t n, uint32_t* rings, uint32_t* weyl,
+                                 uint64_t* pos, cudaStream_t s);
+cudaError_t launch_import_states(const State& st, uint32_t first, uint32_t n, const uint32_t* rings,
+                                 const uint32_t* weyl, const uint64_t* pos, uint32_t weyl_on, cudaStream_t s);
 const void* batch_kernel_ptr(int param_set);
 
 // Per parameter set (defined in xg_inst_default.cu / xg_inst_paper.cu).

@@ -67,6 +67,59 @@ cudaError_t launch_transform(int out_kind, const uint32_t* in, uint64_t n, float
     return cudaGetLastError();
 }
 
+// Bulk checkpoint: stream first + k's ring (oldest first), Weyl word and
+// position into rings[k], weyl[k], pos[k].
+__global__ void __launch_bounds__(128) export_states_kernel(State st, uint32_t first, uint32_t n,
+                                                            uint32_t* __restrict__ rings,
+                                                            uint32_t* __restrict__ weyl,
+                                                            uint64_t* __restrict__ pos)
+{
+    const uint32_t k = blockIdx.x;
+    if (k >= n) return;
+    const uint32_t s = first + k;
+    const uint32_t* src = st.win + (size_t)s * kWin + (kRingBase - st.pend[s]);
+    for (int w = threadIdx.x; w < 128; w += blockDim.x) rings[(size_t)k * 128 + w] = src[w];
+    if (threadIdx.x == 0) {
+        weyl[k] = st.weyl[s];
+        pos[k] = st.pos[s];
+    }
+}
+
+// Bulk restore: the ring at window[kRingBase, kWin), pend = 0, the Weyl word
+// (0 with the Weyl generator off), and the position when pos is given.
+__global__ void __launch_bounds__(128) import_states_kernel(State st, uint32_t first, uint32_t n,
+                                                            const uint32_t* __restrict__ rings,
+                                                            const uint32_t* __restrict__ weyl,
+                                                            const uint64_t* __restrict__ pos, uint32_t weyl_on)
+{
+    const uint32_t k = blockIdx.x;
+    if (k >= n) return;
+    const uint32_t s = first + k;
+    uint32_t* dst = st.win + (size_t)s * kWin + kRingBase;
+    for (int w = threadIdx.x; w < 128; w += blockDim.x) dst[w] = rings[(size_t)k * 128 + w];
+    if (threadIdx.x == 0) {
+        st.weyl[s] = weyl_on ? weyl[k] : 0u;
+        st.pend[s] = 0;
+        if (pos) st.pos[s] = pos[k];
+    }
+}
+
+cudaError_t launch_export_states(const State& st, uint32_t first, uint32_t n, uint32_t* rings, uint32_t* weyl,
+                                 uint64_t* pos, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    export_states_kernel<<<n, 128, 0, s>>>(st, first, n, rings, weyl, pos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_states(const State& st, uint32_t first, uint32_t n, const uint32_t* rings,
+                                 const uint32_t* weyl, const uint64_t* pos, uint32_t weyl_on, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    import_states_kernel<<<n, 128, 0, s>>>(st, first, n, rings, weyl, pos, weyl_on);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_seed(int param_set, const State& st, const uint32_t* d_seeds, uint32_t first,
                         uint32_t count, cudaStream_t s)
 {

@@ -383,6 +383,57 @@ xg_status xg_set_state(xg_ctx* ctx, uint32_t stream, const uint32_t* ring, uint3
     return XG_OK;
 }
 
+xg_status xg_get_states(xg_ctx* ctx, uint32_t first, uint32_t count, uint32_t* rings, uint32_t* weyl,
+                        uint64_t* pos)
+{
+    if (xg_status s = check_ctx(ctx)) return s;
+    Ctx* c = ctx;
+    if ((uint64_t)first + count > c->n) return fail(XG_EINVAL, "streams [%u, %u) out of range", first, first + count);
+    if (count == 0) return XG_OK;
+    if (!rings || !weyl) return fail(XG_EINVAL, "null output");
+    std::lock_guard<std::mutex> lk(c->mu);
+    const size_t rb = (size_t)count * 128 * 4, wb = (size_t)count * 4, pb = (size_t)count * 8;
+    char* d = nullptr;
+    XG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), rb + wb + pb + 16, c->stream), "cudaMallocAsync(states)");
+    uint32_t* d_rings = reinterpret_cast<uint32_t*>(d);
+    uint32_t* d_weyl = reinterpret_cast<uint32_t*>(d + rb);
+    uint64_t* d_pos = reinterpret_cast<uint64_t*>(d + (rb + wb + 7) / 8 * 8);
+    cudaError_t e = xg::launch_export_states(c->st, first, count, d_rings, d_weyl, d_pos, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rings, d_rings, rb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(weyl, d_weyl, wb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && pos) e = cudaMemcpyAsync(pos, d_pos, pb, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? XG_OK : cuda_fail(e, "xg_get_states");
+}
+
+xg_status xg_set_states(xg_ctx* ctx, uint32_t first, uint32_t count, const uint32_t* rings, const uint32_t* weyl,
+                        const uint64_t* pos)
+{
+    if (xg_status s = check_ctx(ctx)) return s;
+    Ctx* c = ctx;
+    if ((uint64_t)first + count > c->n) return fail(XG_EINVAL, "streams [%u, %u) out of range", first, first + count);
+    if (count == 0) return XG_OK;
+    if (!rings || !weyl) return fail(XG_EINVAL, "null input");
+    if (c->server) return fail(XG_EINVAL, "the request server owns this context; stop it first");
+    std::lock_guard<std::mutex> lk(c->mu);
+    const size_t rb = (size_t)count * 128 * 4, wb = (size_t)count * 4, pb = (size_t)count * 8;
+    char* d = nullptr;
+    XG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), rb + wb + pb + 16, c->stream), "cudaMallocAsync(states)");
+    uint32_t* d_rings = reinterpret_cast<uint32_t*>(d);
+    uint32_t* d_weyl = reinterpret_cast<uint32_t*>(d + rb);
+    uint64_t* d_pos = reinterpret_cast<uint64_t*>(d + (rb + wb + 7) / 8 * 8);
+    cudaError_t e = cudaMemcpyAsync(d_rings, rings, rb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_weyl, weyl, wb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && pos) e = cudaMemcpyAsync(d_pos, pos, pb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = xg::launch_import_states(c->st, first, count, d_rings, d_weyl, pos ? d_pos : nullptr, c->weyl_on,
+                                     c->stream);
+    cudaFreeAsync(d, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host arrays are caller-owned
+    return e == cudaSuccess ? XG_OK : cuda_fail(e, "xg_set_states");
+}
+
 xg_status xg_generate_u32(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uint64_t n, uint32_t* out, uint64_t ld)
 {
     return generate_common(ctx, xg::kU32, first, nstreams, n, out, ld);

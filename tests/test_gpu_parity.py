@@ -181,6 +181,36 @@ def test_state_checkpoint_matches_oracle_state():
         assert np.array_equal(a[0], g.u32(700))
 
 
+def test_bulk_checkpoint_restore_and_migrate():
+    """xg_get_states / xg_set_states: the checkpoint equals the oracle's
+    state, restoring it replays the same continuation, and loading it into
+    another context (other seeds) makes that one continue identically."""
+    S = 300
+    seeds = W.seeds(S, start=901)
+    with Streams(S, seeds=seeds) as st:
+        st.uniform(1777)                                   # pend != 0 afterwards
+        ck = st.checkpoint()
+        for i in (0, 7, S - 1):
+            g = O.Xorgens.param_set(0).seed(int(seeds[i]))
+            g.u32(1777)
+            ring, w = g.get_state()
+            assert np.array_equal(ck["rings"][i], ring) and int(ck["weyl"][i]) == w
+        assert np.all(ck["pos"] == 1777)
+        ref = u32np(st.u32(2049))
+        st.restore(ck)
+        assert np.array_equal(u32np(st.u32(2049)), ref)
+        part = st.checkpoint(first=100, count=50)
+    with Streams(S, seeds=W.seeds(S, start=5)) as other:
+        other.restore(ck)
+        assert np.array_equal(u32np(other.u32(2049)), ref)
+        assert np.all(other.checkpoint()["pos"] == 1777 + 2049)
+        other.restore(part, first=0, positions=False)      # a slice into other streams
+        got = u32np(other.u32(10, first=0, count=50))
+    g = O.Xorgens.param_set(0).seed(int(seeds[100]))
+    g.u32(1777 + 2049)                                     # where the slice was taken
+    assert np.array_equal(got[0], g.u32(10))
+
+
 def test_reseed_equals_fresh_context():
     seeds = W.seeds(20)
     with Streams(20, seeds=seeds) as st:
