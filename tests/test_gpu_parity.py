@@ -403,3 +403,35 @@ def test_argument_errors():
         a = u32np(st.u32(10))
     ref = O.streams(W.seeds(10), 10)
     assert np.array_equal(a, ref)
+
+
+def test_single_stream_beyond_2p32_words():
+    """One call of 2^32 + 5 words on one stream (16 GiB; the counts pass
+    32 bits): the head equals the oracle, the tail equals a stream jumped
+    to the same place, and the position is the whole count."""
+    n = (1 << 32) + 5
+    with Streams(1, seeds=[77]) as st:
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        st.u32(n, out=out.view(1, n))
+        head = u32np(out[:1024])
+        tail = u32np(out[n - 1024:])
+        pos = int(st.checkpoint()["pos"][0])
+        del out
+    assert pos == n
+    assert np.array_equal(head, O.Xorgens.param_set(0).seed(77).u32(1024))
+    with Streams(1, seeds=[77]) as j:
+        j.jump(n - 1024)
+        assert np.array_equal(u32np(j.u32(1024))[0], tail)
+    torch.cuda.empty_cache()
+
+
+def test_four_million_streams():
+    """2^22 streams in one context (3.3 GB of state): seeding and a short
+    call on all of them; the last streams equal the oracle."""
+    S = 1 << 22
+    seeds = np.arange(1, S + 1, dtype=np.uint32)
+    with Streams(S, seeds=seeds) as st:
+        got = u32np(st.u32(40))
+    for i in (0, S // 2 + 3, S - 1):
+        assert np.array_equal(got[i], O.streams([int(seeds[i])], 40)[0]), i
+    torch.cuda.empty_cache()
