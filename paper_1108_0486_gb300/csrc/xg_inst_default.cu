@@ -15,11 +15,6 @@ cudaError_t launch_gen_default(int cfg, int out_kind, bool vec, int block, const
     return launch_gen_impl<ParamsDefault>(cfg, out_kind, vec, block, a, s);
 }
 
-cudaError_t launch_batch_default(const BatchArgs& a, unsigned grid, cudaStream_t s)
-{
-    return launch_batch_impl<ParamsDefault>(a, grid, s);
-}
-
 const void* batch_kernel_ptr_default() { return batch_kernel_ptr<ParamsDefault>(); }
 
 }  // namespace xg

@@ -15,11 +15,6 @@ cudaError_t launch_gen_paper(int cfg, int out_kind, bool vec, int block, const G
     return launch_gen_impl<ParamsPaper>(cfg, out_kind, vec, block, a, s);
 }
 
-cudaError_t launch_batch_paper(const BatchArgs& a, unsigned grid, cudaStream_t s)
-{
-    return launch_batch_impl<ParamsPaper>(a, grid, s);
-}
-
 const void* batch_kernel_ptr_paper() { return batch_kernel_ptr<ParamsPaper>(); }
 
 }  // namespace xg

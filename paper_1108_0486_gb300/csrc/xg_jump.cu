@@ -90,47 +90,6 @@ __global__ void __launch_bounds__(64) gf2_apply_kernel(const uint64_t* __restric
     }
 }
 
-// Partial products for few states: block (x, y) handles states
-// [16x, 16x+16) of the list and input words [y*wchunk, (y+1)*wchunk); its
-// XOR goes into tmp[j] (zeroed beforehand) with 64-bit atomic XORs.
-__global__ void __launch_bounds__(64) gf2_apply_partial_kernel(const uint64_t* __restrict__ C,
-                                                               const uint64_t* __restrict__ vecs,
-                                                               const uint32_t* __restrict__ idx, uint32_t n,
-                                                               uint64_t* __restrict__ tmp, int wchunk)
-{
-    __shared__ uint64_t vin[kApplyVecs][kWords64];
-    const int t = threadIdx.x;
-    const uint32_t base = blockIdx.x * kApplyVecs;
-    const int nv = (int)umin((uint32_t)kApplyVecs, n - base);
-    const int w0 = blockIdx.y * wchunk, w1 = min(kWords64, w0 + wchunk);
-    for (int v = 0; v < nv; ++v) vin[v][t] = vecs[(size_t)idx[base + v] * kWords64 + t];
-    __syncthreads();
-    uint64_t acc[kApplyVecs];
-#pragma unroll
-    for (int v = 0; v < kApplyVecs; ++v) acc[v] = 0;
-    for (int w = w0; w < w1; ++w) {
-        uint64_t bits[kApplyVecs];
-        uint64_t any = 0;
-#pragma unroll
-        for (int v = 0; v < kApplyVecs; ++v) {
-            bits[v] = v < nv ? vin[v][w] : 0ull;
-            any |= bits[v];
-        }
-        while (any) {
-            const int b = __ffsll((long long)any) - 1;
-            any &= any - 1;
-            const uint64_t col = C[(size_t)(w * 64 + b) * kWords64 + t];
-#pragma unroll
-            for (int v = 0; v < kApplyVecs; ++v) acc[v] ^= col & (0ull - ((bits[v] >> b) & 1ull));
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < kApplyVecs; ++v)
-        if (v < nv && acc[v])
-            atomicXor(reinterpret_cast<unsigned long long*>(&tmp[(size_t)(base + v) * kWords64 + t]),
-                      (unsigned long long)acc[v]);
-}
-
 // dst[i] ^= C src[i] for n (src, dst) pairs, dst zeroed beforehand.  Block
 // (x, y): pairs [16x, 16x+16), columns [y*cols, (y+1)*cols); 128 threads,
 // thread t owns 32-bit word t of every result.  Columns go four at a time:
@@ -186,13 +145,6 @@ __global__ void zero_listed_kernel(uint32_t* __restrict__ rings, const uint32_t*
 {
     const uint32_t j = blockIdx.x;
     if (j < n) rings[(size_t)idx[j] * kR + threadIdx.x] = 0u;
-}
-
-__global__ void copy_listed_kernel(const uint64_t* __restrict__ tmp, uint64_t* __restrict__ vecs,
-                                   const uint32_t* __restrict__ idx, uint32_t n)
-{
-    const uint32_t j = blockIdx.x;
-    if (j < n) vecs[(size_t)idx[j] * kWords64 + threadIdx.x] = tmp[(size_t)j * kWords64 + threadIdx.x];
 }
 
 // Copy each listed stream's current ring (window at its pend offset) into
@@ -281,27 +233,6 @@ const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg
         return nullptr;
     }
     return T.mat[k];
-}
-
-cudaError_t launch_gf2_apply(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx, cudaStream_t s)
-{
-    if (n == 0) return cudaSuccess;
-    gf2_apply_kernel<<<(n + kApplyVecs - 1) / kApplyVecs, 64, 0, s>>>(C, vecs, vecs, n, d_idx);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gf2_apply_listed(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx,
-                                    uint64_t* d_tmp, int sm_count, cudaStream_t s)
-{
-    if (n == 0) return cudaSuccess;
-    const uint32_t groups = (n + kApplyVecs - 1) / kApplyVecs;
-    int chunks = (int)std::min<uint32_t>(64, std::max<uint32_t>(1, (uint32_t)(4 * sm_count) / groups));
-    while (64 % chunks) --chunks;
-    cudaError_t e = cudaMemsetAsync(d_tmp, 0, (size_t)n * kWords64 * 8, s);
-    if (e != cudaSuccess) return e;
-    gf2_apply_partial_kernel<<<dim3(groups, chunks), 64, 0, s>>>(C, vecs, d_idx, n, d_tmp, 64 / chunks);
-    copy_listed_kernel<<<n, 64, 0, s>>>(d_tmp, vecs, d_idx, n);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_gf2_apply_pairs(const uint64_t* C, uint32_t* rings, uint32_t n, const uint32_t* d_src,

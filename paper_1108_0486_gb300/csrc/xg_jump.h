@@ -15,15 +15,6 @@ constexpr int kMaxPow = 64;  // C_k = M^(2^k), k < 64
 // stream s; 2 MiB each, kept until the process exits).  Null on failure.
 const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg_status* st);
 
-// vecs[i] = C vecs[i] for the n 512-byte states listed in d_idx (or all).
-cudaError_t launch_gf2_apply(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx,
-                             cudaStream_t s);
-
-// The same for a few listed states at low latency: the columns are split
-// across blocks and combined with atomic XOR into d_tmp (n x 512 bytes).
-cudaError_t launch_gf2_apply_listed(const uint64_t* C, uint64_t* vecs, uint32_t n, const uint32_t* d_idx,
-                                    uint64_t* d_tmp, int sm_count, cudaStream_t s);
-
 // rings[d_dst[i]] ^= C rings[d_src[i]] for n pairs (destinations distinct,
 // not among the sources, zeroed beforehand); rings are 128-word states.
 cudaError_t launch_gf2_apply_pairs(const uint64_t* C, uint32_t* rings, uint32_t n, const uint32_t* d_src,

@@ -480,13 +480,6 @@ cudaError_t launch_gen_cfg(int out_kind, bool vec, int block, const GenArgs& a, 
 }
 
 template <class P>
-cudaError_t launch_batch_impl(const BatchArgs& a, unsigned grid, cudaStream_t s)
-{
-    batch_kernel<P><<<grid, 128, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <class P>
 const void* batch_kernel_ptr()
 {
     return reinterpret_cast<const void*>(&batch_kernel<P>);

@@ -112,7 +112,6 @@ cudaError_t launch_gen(int param_set, int cfg, int out_kind, bool vec, int block
 cudaError_t launch_transform(int out_kind, const uint32_t* in, uint64_t n, float* out,
                              cudaStream_t s);
 
-cudaError_t launch_batch(int param_set, const BatchArgs& a, unsigned grid, cudaStream_t s);
 // Bulk checkpoint and restore of streams [first, first + n) (128-word rings).
 cudaError_t launch_export_states(const State& st, uint32_t first, uint32_t n, uint32_t* rings, uint32_t* weyl,
                                  uint64_t* pos, cudaStream_t s);
@@ -125,8 +124,6 @@ cudaError_t launch_seed_default(const State&, const uint32_t*, uint32_t, uint32_
 cudaError_t launch_seed_paper(const State&, const uint32_t*, uint32_t, uint32_t, cudaStream_t);
 cudaError_t launch_gen_default(int cfg, int out_kind, bool vec, int block, const GenArgs&, cudaStream_t);
 cudaError_t launch_gen_paper(int cfg, int out_kind, bool vec, int block, const GenArgs&, cudaStream_t);
-cudaError_t launch_batch_default(const BatchArgs&, unsigned grid, cudaStream_t);
-cudaError_t launch_batch_paper(const BatchArgs&, unsigned grid, cudaStream_t);
 const void* batch_kernel_ptr_default();
 const void* batch_kernel_ptr_paper();
 

@@ -134,11 +134,6 @@ cudaError_t launch_gen(int param_set, int cfg, int out_kind, bool vec, int block
                           : launch_gen_default(cfg, out_kind, vec, block, a, s);
 }
 
-cudaError_t launch_batch(int param_set, const BatchArgs& a, unsigned grid, cudaStream_t s)
-{
-    return param_set == 1 ? launch_batch_paper(a, grid, s) : launch_batch_default(a, grid, s);
-}
-
 const void* batch_kernel_ptr(int param_set)
 {
     return param_set == 1 ? batch_kernel_ptr_paper() : batch_kernel_ptr_default();
