@@ -72,7 +72,7 @@ enum { XG_PARAMS_DEFAULT = 0, XG_PARAMS_PAPER = 1 };
  * param_set: XG_PARAMS_DEFAULT or XG_PARAMS_PAPER.  weyl_on: 1 for Eq. (1),
  * 0 to output the GF(2)-linear part x_k alone (for testing).  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream) owned by the caller; it must
- * outlive the context.  Allocates the device state: 776 bytes per stream. */
+ * outlive the context.  Allocates the device state: 784 bytes per stream. */
 xg_status xg_create_streams(xg_ctx** out, uint32_t n_streams, uint32_t param_set,
                             uint32_t weyl_on, void* cuda_stream);
 
@@ -165,7 +165,9 @@ typedef struct {
 
 /* Run n_items generation calls with ONE launch of the persistent batch
  * kernel, replayed from a CUDA graph (a copy of the batch description into
- * device scratch, then the kernel).  Items may have different types and very
+ * device scratch, then the kernel); when long calls are cut into pieces (see
+ * xg_set_batch_split), a jump-ahead prologue of a few small launches comes
+ * first.  Items may have different types and very
  * different lengths.  Items of the same stream run in array order, exactly as
  * consecutive xg_generate_* calls would; different streams run concurrently,
  * one warp per stream, the longest stream first.  Asynchronous on the
