@@ -13,6 +13,7 @@
 //              that arrive while others run start as soon as a lane frees.
 //   complete-> the kernel fences each request's stores and sets its flag in
 //              mapped pinned host memory; xg_poll reads it directly.
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <chrono>
@@ -27,7 +28,6 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
-#include <unordered_set>
 #include <vector>
 
 #include "xg_batch.h"
@@ -43,7 +43,12 @@ static uint64_t now_ns()
         .count();
 }
 
-// First-fit sub-allocator over one device slab; free blocks coalesce.
+// Sub-allocator over one device slab in O(1) per call: two-level segregated
+// free lists (size classes of 16 per power of two, with bitmaps to find the
+// smallest non-empty class that fits), blocks split on allocation and merged
+// with free neighbours on release (physical neighbours are linked, so no
+// search).  Block records live on the host; a request keeps its block's
+// handle.  Sizes are in 256-byte units.
 class DevicePool {
 public:
     ~DevicePool()
@@ -58,72 +63,152 @@ public:
             base_ = nullptr;
             return fail(XG_ENOMEM, "server pool: cudaMalloc(%zu) failed", cap_);
         }
-        free_.clear();
-        by_size_.clear();
-        add_free(0, cap_);
+        blk_.clear();
+        spare_.clear();
+        fl_map_ = 0;
+        for (int f = 0; f < kFl; ++f) {
+            sl_map_[f] = 0;
+            for (int t = 0; t < kSl; ++t) heads_[f][t] = kNil;
+        }
+        const uint32_t b = new_block();
+        blk_[b] = Block{0, cap_ / kAlign, kNil, kNil, kNil, kNil, true};
+        insert_free(b);
         return XG_OK;
     }
-    // Best fit in O(log n): the smallest free block that holds the request.
-    void* alloc(size_t bytes)
+    void* alloc(size_t bytes, uint32_t* handle)
     {
-        bytes = (bytes + kAlign - 1) / kAlign * kAlign;
-        auto it = by_size_.lower_bound(bytes);
-        if (it == by_size_.end()) return nullptr;
-        const size_t sz = it->first, off = it->second;
-        by_size_.erase(it);
-        free_.erase(off);
-        if (sz > bytes) add_free(off + bytes, sz - bytes);
-        used_[off] = bytes;
-        return base_ + off;
+        const uint64_t u = std::max<uint64_t>(1, (bytes + kAlign - 1) / kAlign);
+        const uint32_t b = find_fit(u);
+        if (b == kNil) return nullptr;
+        remove_free(b);
+        if (blk_[b].units > u) {  // split off the rest as a free block
+            const uint32_t r = new_block();
+            Block& x = blk_[b];
+            blk_[r] = Block{x.off + u, x.units - u, b, x.next_phys, kNil, kNil, true};
+            if (x.next_phys != kNil) blk_[x.next_phys].prev_phys = r;
+            x.next_phys = r;
+            x.units = u;
+            insert_free(r);
+        }
+        blk_[b].free = false;
+        *handle = b;
+        return base_ + blk_[b].off * kAlign;
     }
-    // Return a block, merging it with free neighbours.
-    void release(void* p)
+    void release(uint32_t b)
     {
-        size_t off = static_cast<char*>(p) - base_;
-        auto u = used_.find(off);
-        if (u == used_.end()) return;
-        size_t sz = u->second;
-        used_.erase(u);
-        auto next = free_.lower_bound(off);
-        if (next != free_.end() && off + sz == next->first) {
-            sz += next->second;
-            drop_size(next->second, next->first);
-            next = free_.erase(next);
+        if (b >= blk_.size() || blk_[b].free) return;
+        blk_[b].free = true;
+        const uint32_t n = blk_[b].next_phys;
+        if (n != kNil && blk_[n].free) {  // absorb the next block
+            remove_free(n);
+            blk_[b].units += blk_[n].units;
+            blk_[b].next_phys = blk_[n].next_phys;
+            if (blk_[n].next_phys != kNil) blk_[blk_[n].next_phys].prev_phys = b;
+            spare_.push_back(n);
         }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                off = prev->first;
-                sz += prev->second;
-                drop_size(prev->second, prev->first);
-                free_.erase(prev);
-            }
+        const uint32_t p = blk_[b].prev_phys;
+        if (p != kNil && blk_[p].free) {  // be absorbed by the previous block
+            remove_free(p);
+            blk_[p].units += blk_[b].units;
+            blk_[p].next_phys = blk_[b].next_phys;
+            if (blk_[b].next_phys != kNil) blk_[blk_[b].next_phys].prev_phys = p;
+            spare_.push_back(b);
+            insert_free(p);
+            return;
         }
-        add_free(off, sz);
+        insert_free(b);
     }
     size_t capacity() const { return cap_; }
 
 private:
     static constexpr size_t kAlign = 256;
+    static constexpr int kSlBits = 4, kSl = 1 << kSlBits, kFl = 64;
+    static constexpr uint32_t kNil = 0xFFFFFFFFu;
+    struct Block {
+        uint64_t off, units;           // in kAlign units
+        uint32_t prev_phys, next_phys;  // neighbours in address order
+        uint32_t prev_free, next_free;  // free list of its class
+        bool free;
+    };
+    // Class of a size: sizes below 16 units exactly; above, 16 classes per
+    // power of two.
+    static void mapping(uint64_t u, int& f, int& t)
+    {
+        if (u < (uint64_t)kSl) {
+            f = 0;
+            t = (int)u;
+            return;
+        }
+        const int msb = 63 - __builtin_clzll(u);
+        f = msb - kSlBits + 1;
+        t = (int)((u >> (msb - kSlBits)) & (kSl - 1));
+    }
+    uint32_t new_block()
+    {
+        if (!spare_.empty()) {
+            const uint32_t b = spare_.back();
+            spare_.pop_back();
+            return b;
+        }
+        blk_.push_back(Block{});
+        return (uint32_t)(blk_.size() - 1);
+    }
+    void insert_free(uint32_t b)
+    {
+        int f, t;
+        mapping(blk_[b].units, f, t);
+        blk_[b].prev_free = kNil;
+        blk_[b].next_free = heads_[f][t];
+        if (heads_[f][t] != kNil) blk_[heads_[f][t]].prev_free = b;
+        heads_[f][t] = b;
+        sl_map_[f] |= 1u << t;
+        fl_map_ |= uint64_t(1) << f;
+    }
+    void remove_free(uint32_t b)
+    {
+        int f, t;
+        mapping(blk_[b].units, f, t);
+        const uint32_t p = blk_[b].prev_free, n = blk_[b].next_free;
+        if (p != kNil) blk_[p].next_free = n;
+        else heads_[f][t] = n;
+        if (n != kNil) blk_[n].prev_free = p;
+        if (heads_[f][t] == kNil) {
+            sl_map_[f] &= ~(1u << t);
+            if (!sl_map_[f]) fl_map_ &= ~(uint64_t(1) << f);
+        }
+    }
+    // A free block of at least u units from the smallest class whose every
+    // block fits (u rounded up to its class's upper bound), or kNil.
+    uint32_t find_fit(uint64_t u) const
+    {
+        uint64_t r = u;
+        if (u >= (uint64_t)kSl) r = u + (uint64_t(1) << (63 - __builtin_clzll(u) - kSlBits)) - 1;
+        int f, t;
+        mapping(r, f, t);
+        uint32_t bits = f < kFl ? sl_map_[f] & (~0u << t) : 0u;
+        if (!bits && f + 1 < kFl) {
+            const uint64_t fb = fl_map_ & (~uint64_t(0) << (f + 1));
+            if (fb) {
+                f = __builtin_ctzll(fb);
+                bits = sl_map_[f];
+            }
+        }
+        if (bits) return heads_[f][__builtin_ctz(bits)];
+        // no class is certain to fit: look through u's own class (its blocks
+        // may still be large enough), a bounded first fit
+        mapping(u, f, t);
+        int seen = 0;
+        for (uint32_t b = heads_[f][t]; b != kNil && seen < 256; b = blk_[b].next_free, ++seen)
+            if (blk_[b].units >= u) return b;
+        return kNil;
+    }
     char* base_ = nullptr;
     size_t cap_ = 0;
-    void add_free(size_t off, size_t sz)
-    {
-        free_[off] = sz;
-        by_size_.emplace(sz, off);
-    }
-    void drop_size(size_t sz, size_t off)
-    {
-        auto r = by_size_.equal_range(sz);
-        for (auto it = r.first; it != r.second; ++it)
-            if (it->second == off) {
-                by_size_.erase(it);
-                return;
-            }
-    }
-    std::map<size_t, size_t> free_;            // offset -> size
-    std::multimap<size_t, size_t> by_size_;    // size -> offset
-    std::unordered_map<size_t, size_t> used_;
+    std::vector<Block> blk_;
+    std::vector<uint32_t> spare_;
+    uint32_t heads_[kFl][kSl];
+    uint32_t sl_map_[kFl] = {};
+    uint64_t fl_map_ = 0;
 };
 
 struct Ticket {
@@ -132,12 +217,36 @@ struct Ticket {
     xg_request req{};
     void* out = nullptr;
     bool pooled = false;
+    uint32_t pool_block = 0;  // the pool's handle of its output (when pooled)
     size_t bytes = 0;
     uint32_t slot = 0;
     uint32_t expected = 1;      // completion increments: 1, or the pieces it was cut into
     std::atomic<int> state{0};  // kQueued, kRunning, kDone, kFailed
     uint64_t t_submit = 0, t_launch = 0;
     std::atomic<uint64_t> t_done{0};
+    std::shared_ptr<Ticket> next_in_stream;  // the stream's queue (scheduler thread only)
+};
+
+// A stream's queue of admitted requests (an intrusive list through the
+// tickets, so queueing allocates nothing) and whether one of its requests
+// is on the GPU.
+struct StreamQueue {
+    std::shared_ptr<Ticket> head;
+    Ticket* tail = nullptr;
+    bool busy = false;
+    void push(const std::shared_ptr<Ticket>& t)
+    {
+        if (tail) tail->next_in_stream = t;
+        else head = t;
+        tail = t.get();
+    }
+    std::shared_ptr<Ticket> pop()
+    {
+        std::shared_ptr<Ticket> t = std::move(head);
+        head = std::move(t->next_in_stream);
+        if (!head) tail = nullptr;
+        return t;
+    }
 };
 
 enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
@@ -161,6 +270,8 @@ public:
         std::memset(h_flags_, 0, nflags * 4);
         if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_flags_), h_flags_, 0) != cudaSuccess)
             return fail(XG_ECUDA, "server: cudaHostGetDevicePointer failed");
+        queues_.assign(c_->n, StreamQueue());
+        tickets_.reserve(size_t(1) << 16);
         lanes_.resize(cfg_.lanes);
         for (auto& l : lanes_) {
             l.launcher = std::make_unique<BatchLauncher>();
@@ -233,7 +344,7 @@ public:
         if (r.d_out) {
             t->out = r.d_out;
         } else {
-            t->out = pool_.alloc(t->bytes);
+            t->out = pool_.alloc(t->bytes, &t->pool_block);
             if (!t->out) {
                 ++refused_;
                 return fail(XG_EAGAIN, "admission refused: no pool block of %zu bytes", t->bytes);
@@ -281,8 +392,9 @@ public:
             if (outstanding_ + bytes > cfg_.mem_cap_bytes) break;
             void* out = reqs[k].d_out;
             const bool pooled = out == nullptr;
+            uint32_t block = 0;
             if (pooled) {
-                out = pool_.alloc(bytes);
+                out = pool_.alloc(bytes, &block);
                 if (!out) break;
             }
             made.push_back(std::make_shared<Ticket>());
@@ -291,6 +403,7 @@ public:
             t->bytes = bytes;
             t->out = out;
             t->pooled = pooled;
+            t->pool_block = block;
             outstanding_ += t->bytes;
             t->id = next_id_++;
             t->seq = t->id;
@@ -374,7 +487,7 @@ public:
             if (!(t.state.load() == kRunning && *f >= t.expected))
                 return fail(XG_EINVAL, "ticket %llu still in flight", (unsigned long long)id);
         }
-        if (t.pooled) pool_.release(t.out);
+        if (t.pooled) pool_.release(t.pool_block);
         outstanding_ -= t.bytes;
         tickets_.erase(it);
         return XG_OK;
@@ -418,7 +531,7 @@ public:
             c.pad = 0;
             c.d_result = t->out;
             if (release) {
-                if (t->pooled) pool_.release(t->out);
+                if (t->pooled) pool_.release(t->pool_block);
                 outstanding_ -= t->bytes;
                 dropped.push_back(std::move(it->second));
                 tickets_.erase(it);
@@ -496,9 +609,10 @@ private:
             const uint64_t q1 = timed ? now_ns() : 0;
             ++loop_iters_;
             for (auto& t : fresh) {
-                auto& q = fifo_[t->req.stream];
-                q.push_back(t);
-                if (q.size() == 1 && !busy_streams_.count(t->req.stream)) ready_.push({t->seq, t->req.stream});
+                StreamQueue& q = queues_[t->req.stream];
+                const bool was_empty = !q.head;
+                q.push(t);
+                if (was_empty && !q.busy) ready_.push({t->seq, t->req.stream});
                 ++queued_;
                 progress = true;
             }
@@ -563,11 +677,9 @@ private:
                 while (!ready_.empty() && items.size() < cfg_.max_batch) {
                     const uint32_t s = ready_.top().second;
                     ready_.pop();
-                    auto& q = fifo_[s];
-                    auto t = q.front();
-                    q.pop_front();
-                    if (q.empty()) fifo_.erase(s);
-                    busy_streams_.insert(s);
+                    StreamQueue& q = queues_[s];
+                    auto t = q.pop();
+                    q.busy = true;
                     t->slot = (uint32_t)(li * cfg_.max_batch + items.size());
                     t->t_launch = t_launch;
                     items.push_back(HostItem{s, t->req.type, t->req.count, t->out, d_flags_ + t->slot});
@@ -661,9 +773,9 @@ private:
     {
         const uint32_t s = t->req.stream;
         inflight_words_ -= t->req.count;
-        busy_streams_.erase(s);
-        auto it = fifo_.find(s);
-        if (it != fifo_.end() && !it->second.empty()) ready_.push({it->second.front()->seq, s});
+        StreamQueue& q = queues_[s];
+        q.busy = false;
+        if (q.head) ready_.push({q.head->seq, s});
         ++completed_;
         --in_flight_;
         std::lock_guard<std::mutex> dl(done_mu_);
@@ -692,8 +804,7 @@ private:
     uint64_t loop_iters_ = 0, loop_ns_[4] = {0, 0, 0, 0};  // scheduler thread only
     std::vector<TraceRec> trace_;                 // scheduler thread until stop
     // scheduler thread only
-    std::unordered_map<uint32_t, std::deque<std::shared_ptr<Ticket>>> fifo_;
-    std::unordered_set<uint32_t> busy_streams_;
+    std::vector<StreamQueue> queues_;  // one per stream of the context
     std::priority_queue<std::pair<uint64_t, uint32_t>, std::vector<std::pair<uint64_t, uint32_t>>,
                         std::greater<std::pair<uint64_t, uint32_t>>>
         ready_;
