@@ -331,8 +331,9 @@ xg_status xg_get_launch(const xg_ctx* ctx, xg_type type, uint32_t* tpg, uint32_t
 
 /* Autotuner: time every supported (tpg, wpl) with 32, 64, 128 and 256
  * threads per block on a slice of the workload (nstreams streams -- 0 = all
- * -- by up to n_per_stream outputs, at most 2^27 outputs in all), keep the
- * fastest for later calls of this type and return it (outputs may be NULL).
+ * -- by up to n_per_stream outputs, at most 2^28 outputs in all; the median
+ * of five launches each), keep the fastest for later calls of this type and
+ * return it (outputs may be NULL; best_ms is that median).
  * The streams do not advance: their state is saved and restored around the
  * timing runs.  Synchronous; allocates a temporary buffer for the slice. */
 xg_status xg_autotune(xg_ctx* ctx, xg_type type, uint32_t nstreams, uint64_t n_per_stream,

@@ -84,17 +84,22 @@ __device__ __forceinline__ float neg2ln_u1(uint32_t m1)
     return __fmaf_rn(e, kNeg2Ln2Hi, __fmaf_rn(e, kNeg2Ln2Lo, __fmul_rn(-2.0f, lnf)));
 }
 
-// sqrt(L) with one Newton correction of the hardware reciprocal square root.
+// sqrt(L) with one Newton correction of the hardware reciprocal square root
+// (rsqrt.approx with denormals flushed: L is 0 or at least 1.19e-7, and the
+// guard keeps 0 away, so no input is subnormal and the flush changes no result;
+// it spares the subnormal handling around the approximation).
 __device__ __forceinline__ float sqrt_refined(float L)
 {
-    const float y = rsqrtf(fmaxf(L, 0x1p-100f));
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaxf(L, 0x1p-100f)));
     const float r0 = __fmul_rn(L, y);
     const float d = __fmaf_rn(-r0, r0, L);
     return __fmaf_rn(d, __fmul_rn(0.5f, y), r0);
 }
 
 // Tail branch (R > 5, i.e. m1 <= 62, probability 62 * 2^-24 per pair): FP64.
-static __device__ __noinline__ void normal_pair_fp64(uint32_t m1, uint32_t m2, float& z1, float& z2)
+// Inlined: a call here costs the common FP32 path more than the code size.
+static __device__ __forceinline__ void normal_pair_fp64(uint32_t m1, uint32_t m2, float& z1, float& z2)
 {
     const double u1 = (double)m1 * 0x1p-24;
     const double R = sqrt(-2.0 * log(u1));

@@ -524,8 +524,9 @@ xg_status xg_autotune(xg_ctx* ctx, xg_type type, uint32_t nstreams, uint64_t n_p
     if (c->server) return fail(XG_EINVAL, "the request server owns this context; stop it first");
     if (nstreams == 0 || nstreams > c->n) nstreams = c->n;
     if (n_per_stream == 0) return fail(XG_EINVAL, "n_per_stream must be positive");
-    // a slice of the workload: every stream, at most 2^27 outputs in all
-    uint64_t nt = std::min<uint64_t>(n_per_stream, std::max<uint64_t>(256, (uint64_t(1) << 27) / nstreams));
+    // a slice of the workload: every stream, at most 2^28 outputs in all (a
+    // smaller slice ranked block sizes differently from the full size)
+    uint64_t nt = std::min<uint64_t>(n_per_stream, std::max<uint64_t>(256, (uint64_t(1) << 28) / nstreams));
     nt = align_up(nt, 64);
     std::lock_guard<std::mutex> lk(c->mu);
     const size_t state_bytes = (size_t)((char*)(c->st.pos + c->n) - (char*)c->state_mem);
@@ -560,17 +561,22 @@ xg_status xg_autotune(xg_ctx* ctx, xg_type type, uint32_t nstreams, uint64_t n_p
         for (int b : kBlocks) {
             st = enqueue_gen(c, type, 0, nstreams, nt, out, nt, nullptr, c->stream, ci, b);
             if (st != XG_OK) break;
-            cudaEventRecord(e0, c->stream);
-            for (int r = 0; r < 3 && st == XG_OK; ++r)
+            // the median of five timed launches
+            float t[5];
+            for (int r = 0; r < 5 && st == XG_OK; ++r) {
+                cudaEventRecord(e0, c->stream);
                 st = enqueue_gen(c, type, 0, nstreams, nt, out, nt, nullptr, c->stream, ci, b);
-            cudaEventRecord(e1, c->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                st = cuda_fail(cudaGetLastError(), "autotune timing");
-                break;
+                cudaEventRecord(e1, c->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = cuda_fail(cudaGetLastError(), "autotune timing");
+                    break;
+                }
+                t[r] = 0.f;
+                cudaEventElapsedTime(&t[r], e0, e1);
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= 3.f;
+            if (st != XG_OK) break;
+            std::sort(t, t + 5);
+            const float ms = t[2];
             if (ms < best) {
                 best = ms;
                 best_cfg = ci;
