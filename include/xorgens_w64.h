@@ -50,7 +50,7 @@ typedef enum {
 xg_status xg_w64_params(uint32_t* host_rsabcd6, uint64_t* omega);
 
 /* Create n_streams 64-bit generators on the current device, state resident
- * in device memory (96 words + Weyl word + position per stream, ~800 bytes),
+ * in device memory (96 words + Weyl word + position per stream, 788 bytes),
  * all zero until seeded.  weyl_on: 1 for Eq. (1), 0 for the bare recurrence.
  * cuda_stream: the CUDA stream for all work (NULL: legacy default stream). */
 xg_status xg_w64_create(xg_w64_ctx** out, uint32_t n_streams, uint32_t weyl_on, void* cuda_stream);
