@@ -309,6 +309,12 @@ def run_ours(args):
                 "traffic": args.traffic if args.traffic is not None else _traffic(dom_name),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "per_kernel_ms": {"u32": avg_u, "uniform": avg_f}}
+    # context for a write-only kernel: a memset-style write of the same
+    # size (torch's zero_ of the step's u32 buffer, best of five), measured here
+    wbest = min(_time(lambda: buf_u.zero_(), stream, torch, reps=1, warm=1) for _ in range(5))
+    write_gbs = bytes_per_launch / (wbest / 1e3) / 1e9
+    roofline["write_only_reference"] = {"gbs": write_gbs, "how": "torch zero_ of 4 GiB, best of 5",
+                                        "frac_of_it": achieved / write_gbs}
 
     rows = {}
     if not args.quick and rank == 0:

@@ -82,3 +82,28 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         _lib.lib()
+
+
+def test_public_headers_are_plain_c_and_cpp(tmp_path):
+    import shutil
+    for compiler, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")):
+        if not shutil.which(compiler):
+            pytest.skip(f"{compiler} unavailable")
+        for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+            subprocess.run([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                            "-x", lang, f"-I{ROOT}/include", h], check=True)
+
+
+def test_plain_c_client_links_and_gets_host_side_errors(libpath, tmp_path):
+    """A C program linked against the library: argument checks and error
+    reporting work without touching a GPU."""
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("gcc unavailable")
+    exe = str(tmp_path / "c_abi_check")
+    libdir = os.path.dirname(libpath)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", f"-I{ROOT}/include",
+                    os.path.join(ROOT, "tests", "host", "c_abi_check.c"), "-o", exe,
+                    f"-L{libdir}", "-lxorgens_gb300", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
