@@ -450,3 +450,42 @@ def test_server_trace_records_every_batch(tmp_path, monkeypatch):
     rows = [l.split(",") for l in lines[2:]]
     assert len(rows) == batches and sum(int(r[1]) for r in rows) == 24
     assert all(float(r[7]) >= 0 for r in rows)
+
+
+def test_server_with_the_paper_parameter_set():
+    """The request server on a context of the paper's set (128,65,15,14,12,17)
+    gives the oracle's outputs of that set."""
+    seeds = W.seeds(30, start=300)
+    reqs = [(i % 30, KINDS[i % 3], 700 + 53 * i) for i in range(90)]
+    with Streams(30, param_set=1, seeds=seeds) as st:
+        srv = st.serve(lanes=4)
+        tickets = srv.submit_many(reqs)
+        outs = [srv.result(t, k, n).clone() for t, (_, k, n) in zip(tickets, reqs)]
+        for t in tickets:
+            srv.release(t)
+        srv.stop()
+    for (s, k, n), o, ref in zip(reqs, outs, oracle_per_item(seeds, reqs, ps=1)):
+        check(k, o[:n], ref)
+
+
+def test_contexts_on_concurrent_cuda_streams():
+    """Two contexts generating at the same time on their own CUDA streams
+    (and a batch on a third) give the same outputs as alone."""
+    s1, s2, s3 = (torch.cuda.Stream() for _ in range(3))
+    seeds_a, seeds_b = W.seeds(64, start=1), W.seeds(64, start=1000)
+    with Streams(64, seeds=seeds_a, stream=s1) as a, Streams(64, seeds=seeds_b, stream=s2) as b, \
+            Streams(8, seeds=W.seeds(8, start=77), stream=s3) as c:
+        outs_c = [alloc(KINDS[i % 3], 200000 + i) for i in range(8)]
+        with torch.cuda.stream(s1):
+            ua = a.u32(50000)
+        with torch.cuda.stream(s2):
+            nb = b.normal(50000)
+        c.batch([(i, KINDS[i % 3], 200000 + i, outs_c[i]) for i in range(8)])
+        torch.cuda.synchronize()
+        ua, nb = ua.clone(), nb.clone()
+    with Streams(64, seeds=seeds_a) as a2, Streams(64, seeds=seeds_b) as b2:
+        assert torch.equal(ua, a2.u32(50000))
+        assert torch.equal(nb, b2.normal(50000))
+    refs = oracle_per_item(W.seeds(8, start=77), [(i, KINDS[i % 3], 200000 + i) for i in range(8)])
+    for i in range(8):
+        check(KINDS[i % 3], outs_c[i][:200000 + i], refs[i])
