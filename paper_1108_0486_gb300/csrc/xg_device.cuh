@@ -73,14 +73,17 @@ __device__ __forceinline__ float neg2ln_u1(uint32_t m1)
 {
     const float fm = __uint2float_rn(m1);                  // exact (m1 <= 2^24)
     const int bits = __float_as_int(fm);
-    const int k = (bits - 0x3F3504F3) >> 23;               // fm = 2^k f, f in [sqrt(.5), sqrt(2))
-    const float f = __int_as_float(bits - (k << 23));
+    // fm = 2^(k+24) f with f in [sqrt(.5), sqrt(2)); the bias 24 is folded
+    // into the split so that k is already the exponent of u1
+    const int d = bits - (0x3F3504F3 + (24 << 23));
+    const int k = d >> 23;
+    const float f = __int_as_float((d & 0x7FFFFF) + 0x3F3504F3);
     const float t = __fsub_rn(f, 1.0f);                    // exact
     float q = kLogQ[8];
 #pragma unroll
     for (int i = 7; i >= 0; --i) q = __fmaf_rn(q, t, kLogQ[i]);
     const float lnf = __fmaf_rn(__fmul_rn(t, t), q, t);    // ln f
-    const float e = __int2float_rn(k - 24);                // u1 = 2^e f
+    const float e = __int2float_rn(k);                     // u1 = 2^e f
     return __fmaf_rn(e, kNeg2Ln2Hi, __fmaf_rn(e, kNeg2Ln2Lo, __fmul_rn(-2.0f, lnf)));
 }
 
@@ -121,18 +124,23 @@ __device__ __forceinline__ void normal_pair(uint32_t o1, uint32_t o2, float& z1,
     // angle 2 pi u2 = n (pi/2) + (pi/4) x with n = q mod 4, reduced exactly in
     // integers: mm = m2 + 2^21 holds q = mm >> 22 and x 2^21 = (mm mod 2^22) - 2^21
     const uint32_t mm = m2 + (1u << 21);
-    const int rr = (int)(mm & 0x3FFFFFu) - (1 << 21);            // [-2^21, 2^21)
-    const float x = __fmul_rn(__int2float_rn(rr), 0x1p-21f);     // exact
-    const float y = __fmul_rn(x, x);
-    float sp = kSinS[3];
-    sp = __fmaf_rn(sp, y, kSinS[2]);
-    sp = __fmaf_rn(sp, y, kSinS[1]);
-    const float s = __fmaf_rn(x, kSinS[0], __fmaf_rn(x, kSinS0Lo, __fmul_rn(__fmul_rn(x, y), sp)));
-    float cp = kCosC[3];
-    cp = __fmaf_rn(cp, y, kCosC[2]);
-    cp = __fmaf_rn(cp, y, kCosC[1]);
-    cp = __fmaf_rn(cp, y, kCosC[0]);
-    const float c = __fmaf_rn(cp, y, 1.0f);
+    // xq = x/4 = ((mm mod 2^22) - 2^21) 2^-23, exactly: the 22 bits as the
+    // fraction of a number in [1, 2), minus 1.25.  The polynomials run in
+    // yq = xq^2 = y/16 with their coefficients scaled by the matching powers
+    // of two, so every intermediate is the x-form one times a power of two
+    // and rounds identically (all stay far above the subnormal range).
+    const float xq = __fsub_rn(__uint_as_float((mm & 0x3FFFFFu) | 0x3F800000u), 1.25f);
+    const float yq = __fmul_rn(xq, xq);
+    float sp = kSinS[3] * 16384.0f;                                // 64 S(y) in yq
+    sp = __fmaf_rn(sp, yq, kSinS[2] * 1024.0f);
+    sp = __fmaf_rn(sp, yq, kSinS[1] * 64.0f);
+    const float s = __fmaf_rn(xq, kSinS[0] * 4.0f,
+                              __fmaf_rn(xq, kSinS0Lo * 4.0f, __fmul_rn(__fmul_rn(xq, yq), sp)));
+    float cp = kCosC[3] * 65536.0f;                                // 16 C(y) in yq
+    cp = __fmaf_rn(cp, yq, kCosC[2] * 4096.0f);
+    cp = __fmaf_rn(cp, yq, kCosC[1] * 256.0f);
+    cp = __fmaf_rn(cp, yq, kCosC[0] * 16.0f);
+    const float c = __fmaf_rn(cp, yq, 1.0f);
     // (cos, sin) = (c,s), (-s,c), (-c,-s), (s,-c) for n = 0..3: swap when n is
     // odd (bit 22 of mm); the first is negated when bit 1 of n + 1 is set
     // (bit 23 of mm + 2^22), the second when bit 1 of n is (bit 23 of mm)
