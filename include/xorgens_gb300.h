@@ -24,7 +24,11 @@
  *     (pageable or pinned) host memory.  The library never frees caller memory.
  *   - Work is enqueued on the context's CUDA stream and is asynchronous unless
  *     the entry point says otherwise.  Calls on one context must come from one
- *     host thread at a time.
+ *     host thread at a time, except the request server's calls (xg_submit,
+ *     xg_submit_many, xg_poll, xg_wait, xg_release, xg_collect,
+ *     xg_ticket_times, xg_server_stats_get), which several threads may make
+ *     at once while the server runs; xg_server_start and xg_server_stop must
+ *     not overlap any other call on the context.
  *   - Stream positions advance with every call, in call order.  Any split of
  *     a stream's output into consecutive calls concatenates to the same
  *     sequence as one call, for every output type and launch configuration.
@@ -274,7 +278,9 @@ xg_status xg_server_start(xg_ctx* ctx, const xg_server_config* cfg);
 xg_status xg_server_stop(xg_ctx* ctx);
 
 /* Non-blocking.  XG_EAGAIN when admitting the request would put the
- * outstanding output bytes above the cap (retry later, after xg_release). */
+ * outstanding output bytes above the cap (retry later, after xg_release);
+ * XG_EINVAL for a request larger than the cap itself, which could never be
+ * admitted. */
 xg_status xg_submit(xg_ctx* ctx, const xg_request* req, uint64_t* ticket);
 
 /* Non-blocking bulk submission: admits reqs[0 .. n) in order, as n calls of

@@ -331,6 +331,9 @@ public:
         if (r.stream >= c_->n) return fail(XG_EINVAL, "stream %u out of range", r.stream);
         if (r.type > XG_NORMAL_F32) return fail(XG_EINVAL, "unknown type %u", r.type);
         if (r.count == 0) return fail(XG_EINVAL, "empty request");
+        if (r.count > cfg_.mem_cap_bytes / 4)
+            return fail(XG_EINVAL, "request of %llu outputs exceeds the memory cap (%llu bytes): it could never be admitted",
+                        (unsigned long long)r.count, (unsigned long long)cfg_.mem_cap_bytes);
         if (reinterpret_cast<uintptr_t>(r.d_out) & 3u) return fail(XG_EINVAL, "output not 4-byte aligned");
         auto t = std::make_shared<Ticket>();
         t->req = r;
@@ -378,6 +381,9 @@ public:
             if (r.stream >= c_->n) return fail(XG_EINVAL, "request %u: stream %u out of range", i, r.stream);
             if (r.type > XG_NORMAL_F32) return fail(XG_EINVAL, "request %u: unknown type %u", i, r.type);
             if (r.count == 0) return fail(XG_EINVAL, "request %u: empty request", i);
+            if (r.count > cfg_.mem_cap_bytes / 4)
+                return fail(XG_EINVAL, "request %u: %llu outputs exceed the memory cap (%llu bytes)", i,
+                            (unsigned long long)r.count, (unsigned long long)cfg_.mem_cap_bytes);
             if (reinterpret_cast<uintptr_t>(r.d_out) & 3u)
                 return fail(XG_EINVAL, "request %u: output not 4-byte aligned", i);
         }

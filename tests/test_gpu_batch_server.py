@@ -1,6 +1,7 @@
 """Batched persistent kernel and request server against the oracle and
 against the plain one-launch-per-call path."""
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -207,6 +208,86 @@ def test_server_pool_buffers_and_release():
         check(k, r[:n], ref)
 
 
+def test_server_submit_and_collect_on_two_threads():
+    """One thread submits in bulk under a small memory cap (resubmitting the
+    refused tail), another drains completions with xg_collect, copies each
+    pooled result and releases it, as the header allows; every result
+    equals the same request run alone."""
+    from paper_1108_0486_gb300 import _lib as L
+    from paper_1108_0486_gb300.api import device_view
+    rng = np.random.default_rng(21)
+    S = 64
+    seeds = W.seeds(S, start=5)
+    reqs = random_items(rng, S, 400, max_len=60000)
+    got = {}
+    ticket_of = [None] * len(reqs)
+    done_submitting = threading.Event()
+    refused = threading.Event()
+    errors = []
+    with Streams(S, seeds=seeds) as st:
+        srv = st.serve(mem_cap_bytes=2 << 20, lanes=4, max_batch=32)
+        req_of = {}
+        book = threading.Lock()
+
+        def submitter():
+            try:
+                i = 0
+                while i < len(reqs):
+                    # xg_submit_many admits a prefix of the chunk; the cap
+                    # refused the rest, which goes again
+                    with book:   # tickets are recorded before any can be collected
+                        ts = srv.submit_many(reqs[i:i + 16])
+                        for j, t in enumerate(ts):
+                            req_of[t] = i + j
+                            ticket_of[i + j] = t
+                    if len(ts) < len(reqs[i:i + 16]):
+                        refused.set()
+                    if not ts:
+                        time.sleep(0.0002)
+                    i += len(ts)
+            except Exception as e:  # noqa: BLE001 - reported by the main thread
+                errors.append(e)
+            finally:
+                done_submitting.set()
+
+        def collector():
+            try:
+                # start draining once the cap has pushed back (or all is in)
+                while not (refused.is_set() or done_submitting.is_set()):
+                    time.sleep(0.0005)
+                while not (done_submitting.is_set() and len(got) == sum(t is not None for t in ticket_of)):
+                    with book:
+                        comps = srv.collect(64, release=False)
+                    if not comps:
+                        time.sleep(0.0001)
+                    for (t, _, _, _, status, ptr) in comps:
+                        assert status == L.XG_OK
+                        s_, k, n = reqs[req_of[t]]
+                        dt = torch.int32 if k == "u32" else torch.float32
+                        got[t] = device_view(ptr, n, dt).clone()
+                        torch.cuda.synchronize()
+                        srv.release(t)
+            except Exception as e:  # noqa: BLE001
+                errors.append(e)
+
+        th = [threading.Thread(target=submitter), threading.Thread(target=collector)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join(300)
+        stats = srv.stats()
+        srv.stop()
+    assert not errors, errors
+    assert len(got) == len(reqs) and stats["outstanding_bytes"] == 0
+    assert stats["refused"] > 0          # the cap did push back
+    order = np.argsort(np.array(ticket_of, dtype=np.uint64))
+    with Streams(S, seeds=seeds) as alone:
+        for i in order:
+            s_, k, n = reqs[i]
+            ref = alone.generate(k, n, first=s_, count=1)[0, :n]
+            assert torch.equal(got[ticket_of[i]], ref), (i, s_, k, n)
+
+
 def test_server_admission_by_memory():
     from paper_1108_0486_gb300 import XGError, _lib as L
     with Streams(8, seeds=W.seeds(8)) as st:
@@ -215,6 +296,10 @@ def test_server_admission_by_memory():
         with pytest.raises(XGError) as e:
             srv.submit(1, "u32", 100000)
         assert e.value.status == L.XG_EAGAIN
+        # larger than the cap itself: never admissible, so not a retry case
+        with pytest.raises(XGError) as e:
+            srv.submit(2, "u32", 262145)
+        assert e.value.status == L.XG_EINVAL and "cap" in str(e.value)
         srv.wait(t1)
         srv.release(t1)
         t2 = srv.submit(1, "u32", 100000)
