@@ -51,25 +51,45 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic(kernel=None):
-    """ncu DRAM bytes per launch of the dominant kernel, if recorded for the
-    current kernel sources (else None)."""
+def _record(name):
+    """A profiles/ record (key value lines) taken with ncu, if it was taken
+    on the current kernel sources (else None)."""
     import hashlib
     try:
         rec = {}
-        for line in open(os.path.join(ROOT, "profiles", "gen_kernel_traffic.txt")):
+        for line in open(os.path.join(ROOT, "profiles", name)):
             if line.strip() and not line.startswith("#"):
-                k, v = line.split()
-                rec[k] = v
+                k, v = line.split(None, 1)
+                rec[k] = v.strip()
         src = b"".join(open(os.path.join(ROOT, "paper_1108_0486_gb300", "csrc", f), "rb").read()
                        for f in ("xg_device.cuh", "xg_kernels.cuh"))
         if hashlib.sha256(src).hexdigest()[:16] != rec.get("kernel_sources_sha256_16"):
             return None
-        if kernel is not None and rec.get("kernel") != kernel:
-            return None
-        return float(rec["traffic_bytes_per_launch"])
+        return rec
     except Exception:
         return None
+
+
+def _traffic(kernel=None):
+    """ncu DRAM bytes per launch of the dominant kernel, if recorded for the
+    current kernel sources (else None)."""
+    rec = _record("gen_kernel_traffic.txt")
+    if rec is None or (kernel is not None and rec.get("kernel") != kernel):
+        return None
+    return float(rec["traffic_bytes_per_launch"])
+
+
+def _issue_ceiling(sm_count, sm_mhz):
+    """Normals per second at full instruction issue (4 warp instructions per
+    SM per clock) for the recorded instruction count of gen_kernel<normal>,
+    or None when the record does not match the kernel sources."""
+    rec = _record("gen_kernel_normal_issue.txt")
+    if rec is None or not sm_mhz:
+        return None
+    per_normal = float(rec["warp_instructions"]) / float(rec["normals"])
+    return {"normals_per_s": sm_count * 4 * sm_mhz * 1e6 / per_normal,
+            "instructions_per_normal": round(32 * per_normal, 2), "sm_mhz": sm_mhz,
+            "source": "profiles/gen_kernel_normal_issue.txt (ncu smsp__inst_executed.sum, 16384 x 4096 case)"}
 
 
 def _dist():
@@ -319,7 +339,7 @@ def run_ours(args):
     rows = {}
     if not args.quick and rank == 0:
         # the other rows run on one GPU (with N > 1 the other ranks wait)
-        rows = extra_rows(st, stream, torch, peak)
+        rows = extra_rows(st, stream, torch, peak, sm_mhz=clk.get("sm_mhz") or clk.get("sm_max_mhz"))
         rows["batched"] = batched_row(torch, L, stream, peak)
         rows["serving"] = serving_row(torch, L, stream, seconds=args.serve_seconds)
         rows["serving_sweep"] = serving_sweep(torch, L, stream)
@@ -365,9 +385,10 @@ def _time(fn, stream, torch, reps=5, warm=2):
     return sum(ts) / len(ts)
 
 
-def extra_rows(st, stream, torch, peak):
+def extra_rows(st, stream, torch, peak, sm_mhz=None):
     """Other rows of the path on the same streams: normals (2^30 FP32 over
-    16384 streams) and the fused normal sum (no bulk HBM write)."""
+    16384 streams) and the fused normal sum (no bulk HBM write).  The normal
+    row also reports its issue ceiling: normals are instruction-bound."""
     rows = {}
     n = W.NORMALS["n"]
     buf = torch.empty((STREAMS, n), dtype=torch.float32, device="cuda")
@@ -375,6 +396,11 @@ def extra_rows(st, stream, torch, peak):
     rn = STREAMS * n
     rows["normal"] = {"rn_s": rn / (ms / 1e3), "ms": ms,
                       "hbm_frac": rn * 4 / (ms / 1e3) / 1e9 / peak, "launch": st.get_launch("normal")}
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    ceil = _issue_ceiling(sm_count, sm_mhz)
+    if ceil is not None and tuple(rows["normal"]["launch"]) == (32, 2):
+        ceil["frac"] = rows["normal"]["rn_s"] / ceil["normals_per_s"]
+        rows["normal"]["issue_ceiling"] = ceil
     sums = torch.empty(STREAMS, dtype=torch.float32, device="cuda")
     ms = _time(lambda: st.normal_sum(n, out=sums), stream, torch)
     rows["normal_sum_fused"] = {"rn_s": rn / (ms / 1e3), "ms": ms, "hbm_bytes_written": STREAMS * 4}
