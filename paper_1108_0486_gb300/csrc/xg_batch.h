@@ -53,7 +53,7 @@ public:
     // receives how many completion increments each item will produce.
     // min_piece: the shortest piece the automatic choice may cut (a caller
     // that knows the GPU is already busy raises it: cutting buys latency at
-    // the price of jump-ahead work, about 3.4e4 words' worth per piece).
+    // the price of jump-ahead work, about 2.2e4 words' worth per piece).
     xg_status launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s,
                      uint32_t* units_per_item = nullptr, uint64_t min_piece = kMinPiece);
     static constexpr uint64_t kMinPiece = uint64_t(1) << 16;

@@ -583,7 +583,7 @@ private:
 
     // Shortest piece a new batch may cut its calls into, from the words the
     // GPU already has in flight: cutting shortens one call's critical path
-    // but costs jump-ahead work (about 3.4e4 words' worth per piece), which
+    // but costs jump-ahead work (about 2.2e4 words' worth per piece), which
     // only pays while the GPU would otherwise idle.  B is about 1.5 ms of
     // work: 2^18 words for each of 32 warps per SM.
     uint64_t min_piece_for_backlog() const
