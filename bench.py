@@ -438,6 +438,9 @@ def extra_rows(st, stream, torch, peak, sm_mhz=None):
                                "hbm_frac": rn64 * 8 / (ms_f / 1e3) / 1e9 / peak, "launch": tuned64}
     rows["w64_u64"] = {"rn_s": rn64 / (ms_u / 1e3), "ms": ms_u,
                        "hbm_frac": rn64 * 8 / (ms_u / 1e3) / 1e9 / peak, "launch": tuned64u}
+    ms_j = _time(lambda: s64.jump(J), stream, torch)
+    rows["w64_jump_16384_streams"] = {"words": J, "set_bits": bin(J).count("1"), "ms": ms_j,
+                                      "us_per_stream_application": ms_j * 1e3 / (STREAMS * bin(J).count("1"))}
     s64.close()
     del b64
     return rows

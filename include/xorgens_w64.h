@@ -24,8 +24,9 @@
  * device or host outputs, asynchronous on the context's CUDA stream, calls on
  * one context from one host thread at a time, and any split of a stream's
  * outputs into consecutive calls concatenating to one call's output).
- * Contexts of this header are distinct from xg_ctx: batching, jump-ahead and
- * the request server are for the 32-bit generators only.
+ * Contexts of this header are distinct from xg_ctx: batching and the request
+ * server are for the 32-bit generators only; jump-ahead (xg_w64_jump) exists
+ * for both.
  */
 #ifndef XORGENS_W64_H
 #define XORGENS_W64_H
@@ -94,6 +95,16 @@ xg_status xg_w64_set_launch(xg_w64_ctx* ctx, xg_w64_type type, uint32_t tpg, uin
  * saved and restored.  Synchronous.  Outputs may be NULL. */
 xg_status xg_w64_autotune(xg_w64_ctx* ctx, xg_w64_type type, uint32_t nstreams, uint64_t n_per_stream,
                           uint32_t* tpg, uint32_t* wpl, uint32_t* block, float* best_ms);
+
+/* Jump-ahead: advance streams [first, first+nstreams) by `words` positions
+ * without generating them, exactly as if that many words had been drawn.
+ * The recurrence is linear over GF(2) on the 4096-bit ring (Sec. 2), so the
+ * jump is a product of powers M^(2^k) of its transition matrix, one per set
+ * bit of `words`; the Weyl word advances by words * omega mod 2^64 (Sec. 1.5).
+ * The first use of each power builds it on the GPU (2 MiB each, kept until
+ * the process exits).  Synchronous.  Errors: XG_EINVAL for a null context or
+ * a stream range out of bounds, XG_ENOMEM / XG_ECUDA from the device. */
+xg_status xg_w64_jump(xg_w64_ctx* ctx, uint32_t first, uint32_t nstreams, uint64_t words);
 
 #ifdef __cplusplus
 }

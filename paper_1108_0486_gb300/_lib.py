@@ -108,6 +108,7 @@ SIGNATURES = {
     "xg_w64_transform_uniform_f64": [vp, vp, u64, vp],
     "xg_w64_set_launch": [vp, i32, u32, u32, u32],
     "xg_w64_autotune": [vp, i32, u32, u64, P_u32, P_u32, P_u32, ctypes.POINTER(ctypes.c_float)],
+    "xg_w64_jump": [vp, u32, u32, u64],
 }
 _RESTYPES = {"xg_last_error": ctypes.c_char_p, "xg_version": ctypes.c_char_p}
 
@@ -417,6 +418,10 @@ def xg_w64_transform_uniform_f64(ctx, words_ptr, n, out_ptr) -> None:
 
 def xg_w64_set_launch(ctx, out_type, tpg, wpl, block=0) -> None:
     call("xg_w64_set_launch", ctypes.c_void_p(ctx), out_type, tpg, wpl, block)
+
+
+def xg_w64_jump(ctx, first, nstreams, words) -> None:
+    call("xg_w64_jump", ctypes.c_void_p(ctx), first, nstreams, words)
 
 
 def xg_w64_autotune(ctx, out_type, nstreams, n_per_stream):

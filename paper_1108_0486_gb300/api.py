@@ -343,6 +343,11 @@ class Streams64:
     def autotune(self, kind: str, n_per_stream: int, nstreams: int = 0) -> dict:
         return L.xg_w64_autotune(self.ctx, TYPES_W64[kind], nstreams, n_per_stream)
 
+    def jump(self, words: int, first: int = 0, count=None):
+        """Advance streams by `words` positions without generating them."""
+        count = self.n - first if count is None else count
+        L.xg_w64_jump(self.ctx, first, count, words)
+
     def _gen(self, fn, dtype, n, first, count, out, ld):
         count = self.n - first if count is None else count
         if out is None:

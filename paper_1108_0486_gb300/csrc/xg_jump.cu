@@ -19,6 +19,7 @@
 #include "xg_jump.h"
 #include "xg_kernels.cuh"
 #include "xg_runtime.h"
+#include "xg_w64.h"
 
 namespace xg {
 
@@ -193,18 +194,18 @@ struct Tables {
     int built = 0;                // C_0 .. C_{built-1} are valid
 };
 std::mutex g_tab_mu;
-Tables g_tabs[64][2];  // per device, per parameter set
+Tables g_tabs[64][3];  // per device, per matrix family
 }  // namespace
 
 const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg_status* st)
 {
     *st = XG_OK;
-    if (device < 0 || device >= 64 || k < 0 || k >= kMaxPow) {
+    if (device < 0 || device >= 64 || k < 0 || k >= kMaxPow || param_set < 0 || param_set > kJumpSetW64) {
         *st = fail(XG_EINVAL, "jump power %d out of range", k);
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_tab_mu);
-    Tables& T = g_tabs[device][param_set ? 1 : 0];
+    Tables& T = g_tabs[device][param_set];
     const size_t mat_bytes = (size_t)kBits * kWords64 * 8;
     bool built_now = false;
     while (T.built <= k) {
@@ -217,14 +218,16 @@ const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg
             return nullptr;
         }
         if (b == 0) {
-            if (param_set == 1)
+            if (param_set == kJumpSetW64)
+                e = xg64::launch_step_columns(T.mat[0], s);
+            else if (param_set == 1)
                 step_columns_kernel<ParamsPaper><<<kBits / 128, 128, 0, s>>>(reinterpret_cast<uint32_t*>(T.mat[0]));
             else
                 step_columns_kernel<ParamsDefault><<<kBits / 128, 128, 0, s>>>(reinterpret_cast<uint32_t*>(T.mat[0]));
         } else {
             gf2_apply_kernel<<<kBits / kApplyVecs, 64, 0, s>>>(T.mat[b - 1], T.mat[b - 1], T.mat[b], kBits, nullptr);
         }
-        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) {
             *st = cuda_fail(e, "jump table build");
             return nullptr;

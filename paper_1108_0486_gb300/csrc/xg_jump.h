@@ -10,8 +10,11 @@
 namespace xg {
 
 constexpr int kMaxPow = 64;  // C_k = M^(2^k), k < 64
+// Matrix families: the 32-bit parameter sets 0 (default) and 1 (paper), and
+// the 64-bit-word generator.
+constexpr int kJumpSetW64 = 2;
 
-// C_k for a device and parameter set, built on first use (squarings on
+// C_k for a device and matrix family, built on first use (squarings on
 // stream s; 2 MiB each, kept until the process exits).  Null on failure.
 const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg_status* st);
 

@@ -7,7 +7,9 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
+#include "xg_jump.h"
 #include "xg_runtime.h"
 #include "xg_w64.h"
 
@@ -268,6 +270,57 @@ xg_status xg_w64_generate_uniform_f64(xg_w64_ctx* c, uint32_t first, uint32_t ns
                                       uint64_t ld)
 {
     return generate(c, xg64::kUniformF64, first, nstreams, n, out, ld);
+}
+
+xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t words)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if ((uint64_t)first + nstreams > c->n) return fail(XG_EINVAL, "streams out of range");
+    if (nstreams == 0 || words == 0) return XG_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t s = c->stream;
+    int top = 63;
+    while (!((words >> top) & 1)) --top;
+    xg_status st = XG_OK;
+    for (int k = 0; k <= top; ++k)
+        if (((words >> k) & 1) && !xg::jump_matrix(c->device, xg::kJumpSetW64, k, s, &st)) return st;
+    // rings[0, n) hold the states, rings[n, 2n) receive each application;
+    // the halves swap roles after every set bit of words (the shared
+    // four-column table kernel works on 4096-bit states as 128 32-bit words)
+    uint64_t* rings = nullptr;
+    uint32_t* ids = nullptr;   // 0 .. 2n-1
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)2 * nstreams * xg64::kR * 8, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)2 * nstreams * 4, s);
+    if (e != cudaSuccess) {
+        if (rings) cudaFreeAsync(rings, s);
+        return cuda_fail(e, "xg_w64_jump scratch");
+    }
+    std::vector<uint32_t> h((size_t)2 * nstreams);
+    for (uint32_t i = 0; i < 2 * nstreams; ++i) h[i] = i;
+    uint32_t* rings32 = reinterpret_cast<uint32_t*>(rings);
+    const uint32_t* lo_idx = ids;
+    const uint32_t* hi_idx = ids + nstreams;
+    e = cudaMemcpyAsync(ids, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = xg64::launch_gather_rings(c->st, first, nstreams, rings, s);
+    bool in_lo = true;
+    for (int k = 0; k <= top && e == cudaSuccess; ++k) {
+        if (!((words >> k) & 1)) continue;
+        const uint64_t* C = xg::jump_matrix(c->device, xg::kJumpSetW64, k, s, &st);
+        const uint32_t* src = in_lo ? lo_idx : hi_idx;
+        const uint32_t* dst = in_lo ? hi_idx : lo_idx;
+        e = xg::zero_rings(rings32, dst, nstreams, s);
+        if (e == cudaSuccess) e = xg::launch_gf2_apply_pairs(C, rings32, nstreams, src, dst, c->sm_count, s);
+        in_lo = !in_lo;
+    }
+    if (e == cudaSuccess) {
+        const uint64_t* res = in_lo ? rings : rings + (size_t)nstreams * xg64::kR;
+        e = xg64::launch_scatter_rings(c->st, first, nstreams, res, words, c->weyl_on ? xg64::kOmega : 0, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
+    cudaFreeAsync(rings, s);
+    cudaFreeAsync(ids, s);
+    if (e != cudaSuccess) return cuda_fail(e, "xg_w64_jump");
+    return XG_OK;
 }
 
 xg_status xg_w64_transform_uniform_f64(xg_w64_ctx* c, const uint64_t* d_words, uint64_t n, double* d_out)

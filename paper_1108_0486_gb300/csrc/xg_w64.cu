@@ -384,6 +384,73 @@ cudaError_t launch_transform_uniform(const uint64_t* in, uint64_t n, uint64_t* o
     return cudaGetLastError();
 }
 
+// Columns of the transition matrix M of one step (Sec. 2): column j is the
+// state after one step from the unit state e_j (bit j mod 64 of ring word
+// j / 64).  The ring shifts by one word and the new word is
+// x_{k-r}(I+L^a)(I+R^b) xor x_{k-s}(I+L^c)(I+R^d), with x_{k-r} = ring word 0
+// and x_{k-s} = ring word r - s.
+__global__ void __launch_bounds__(128) step_columns_kernel(uint64_t* __restrict__ cols)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kR * 64) return;
+    const int wj = j >> 6, bj = j & 63;
+    uint64_t* out = cols + (size_t)j * kR;
+    for (int w = 0; w < kR - 1; ++w) out[w] = (w + 1 == wj) ? (uint64_t(1) << bj) : 0ull;
+    uint64_t t = (wj == 0) ? (uint64_t(1) << bj) : 0ull;
+    uint64_t u = (wj == kR - kS) ? (uint64_t(1) << bj) : 0ull;
+    t ^= t << kA;
+    t ^= t >> kB;
+    u ^= u << kC;
+    u ^= u >> kD;
+    out[kR - 1] = t ^ u;
+}
+
+cudaError_t launch_step_columns(uint64_t* cols, cudaStream_t s)
+{
+    step_columns_kernel<<<kR * 64 / 128, 128, 0, s>>>(cols);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(64) gather_rings_kernel(State st, uint32_t first, uint32_t n,
+                                                          uint64_t* __restrict__ rings)
+{
+    const uint32_t k = blockIdx.x;
+    if (k >= n) return;
+    const uint32_t s = first + k;
+    const uint64_t* src = st.win + (size_t)s * kWin + (kRingBase - st.pend[s]);
+    rings[(size_t)k * kR + threadIdx.x] = src[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(64) scatter_rings_kernel(State st, uint32_t first, uint32_t n,
+                                                           const uint64_t* __restrict__ rings, uint64_t jump,
+                                                           uint64_t omega)
+{
+    const uint32_t k = blockIdx.x;
+    if (k >= n) return;
+    const uint32_t s = first + k;
+    st.win[(size_t)s * kWin + kRingBase + threadIdx.x] = rings[(size_t)k * kR + threadIdx.x];
+    if (threadIdx.x == 0) {
+        st.weyl[s] += jump * omega;
+        st.pend[s] = 0;
+        st.pos[s] += jump;
+    }
+}
+
+cudaError_t launch_gather_rings(const State& st, uint32_t first, uint32_t n, uint64_t* rings, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    gather_rings_kernel<<<n, kR, 0, s>>>(st, first, n, rings);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rings(const State& st, uint32_t first, uint32_t n, const uint64_t* rings, uint64_t jump,
+                                 uint64_t omega, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    scatter_rings_kernel<<<n, kR, 0, s>>>(st, first, n, rings, jump, omega);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_seed(const State& st, const uint32_t* d_seeds, uint32_t first, uint32_t count,
                         cudaStream_t s)
 {

@@ -57,4 +57,17 @@ cudaError_t launch_seed(const State& st, const uint32_t* d_seeds, uint32_t first
 cudaError_t launch_gen(int cfg, int kind, bool vec, int block, const GenArgs& a, cudaStream_t s);
 cudaError_t launch_transform_uniform(const uint64_t* in, uint64_t n, uint64_t* out, int sms, cudaStream_t s);
 
+// Jump-ahead.  The 64-word ring is a 4096-bit state like the 32-bit sets'
+// 128-word ring (bit j = bit j mod 64 of word j / 64, the same bits as
+// 32-bit word j / 32 on a little-endian device), so the GF(2) matrix powers
+// and their application are shared with the 32-bit generators.
+// Columns of the one-step matrix: column j (64 words) = one step from e_j.
+cudaError_t launch_step_columns(uint64_t* cols, cudaStream_t s);
+// rings[k] = ring of stream first + k (64 words, oldest first).
+cudaError_t launch_gather_rings(const State& st, uint32_t first, uint32_t n, uint64_t* rings, cudaStream_t s);
+// Stream first + k takes rings[k] as its ring (pend = 0), its Weyl word
+// advanced by jump * omega and its position by jump.
+cudaError_t launch_scatter_rings(const State& st, uint32_t first, uint32_t n, const uint64_t* rings, uint64_t jump,
+                                 uint64_t omega, cudaStream_t s);
+
 }  // namespace xg64

@@ -139,3 +139,46 @@ def test_argument_errors(api):
     buf = torch.empty(16, dtype=torch.int32, device="cuda")
     with pytest.raises(L.XGError):   # 4-byte aligned, not 8: refused on the host
         L.xg_w64_generate_u64(st.ctx, 0, 1, 4, buf.data_ptr() + 4, 4)
+
+
+# ---- jump-ahead -------------------------------------------------------------
+
+@pytest.mark.parametrize("J", [1, 31, 32, 33, 64, 1000, 4099, 123457])
+def test_jump_equals_stepping(api, J):
+    """Jumping J words lands where generating J words does (the oracle
+    steps one word at a time), from a position with words pending."""
+    seeds = list(range(300, 337))
+    st = api.Streams64(len(seeds), seeds=seeds)
+    st.u64(5)
+    st.jump(J)
+    got = _u(st.u64(256))
+    ref = O.streams64(seeds, 5 + J + 256)[:, 5 + J:]
+    assert np.array_equal(got, ref)
+
+
+def test_jump_weyl_off_and_subrange(api):
+    """With the Weyl generator off the jump is the raw recurrence's; only
+    the streams named move."""
+    seeds = [21, 22, 23, 24, 25]
+    st = api.Streams64(5, weyl=False, seeds=seeds)
+    st.jump(777, first=1, count=3)
+    got = _u(st.u64(100))
+    for i, s in enumerate(seeds):
+        g = O.Xorgens64(*O.PARAM_SET_W64, weyl=False).seed(s)
+        if 1 <= i <= 3:
+            g.raw(777)
+        assert np.array_equal(got[i], g.raw(100)), i
+
+
+def test_jump_composes_at_large_distances(api):
+    """M^a M^b = M^(a+b) for distances up to 2^63, and the Weyl word
+    advances by the distance times omega mod 2^64: jumping a then b gives
+    the outputs of jumping a + b at once."""
+    seeds = list(range(1, 17))
+    for a, b in ((1 << 40, (1 << 40) + 12345), ((1 << 63) - 1, 1), (3 << 61, 987654321)):
+        x = api.Streams64(16, seeds=seeds)
+        y = api.Streams64(16, seeds=seeds)
+        x.jump(a)
+        x.jump(b)
+        y.jump(a + b)
+        assert np.array_equal(_u(x.u64(300)), _u(y.u64(300)))
