@@ -139,6 +139,13 @@ def test_argument_errors(api):
     buf = torch.empty(16, dtype=torch.int32, device="cuda")
     with pytest.raises(L.XGError):   # 4-byte aligned, not 8: refused on the host
         L.xg_w64_generate_u64(st.ctx, 0, 1, 4, buf.data_ptr() + 4, 4)
+    with pytest.raises(L.XGError) as e:
+        st.jump(5, first=2, count=3)   # streams out of range
+    assert e.value.status == L.XG_EINVAL
+    # a zero jump and an empty range are no-ops
+    st.jump(0)
+    st.jump(12345, first=4, count=0)
+    assert np.array_equal(_u(st.u64(64)), O.streams64([1, 2, 3, 4], 64))
 
 
 # ---- jump-ahead -------------------------------------------------------------
