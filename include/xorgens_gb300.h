@@ -223,6 +223,18 @@ xg_status xg_set_batch_split(xg_ctx* ctx, uint64_t piece_words);
  * 64-bit distance. */
 xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uint64_t words);
 
+/* Seed streams [first, first+count) as consecutive, disjoint blocks of ONE
+ * sequence: stream first + i starts at position i * 2^log2_spacing of the
+ * sequence that xg_seed gives for `seed` (its ring, Weyl word and position
+ * are those of that sequence there), so no two of them draw a common word
+ * until one has drawn 2^log2_spacing words -- the independent subsequences
+ * of Sec. 2 taken from one period instead of from different seeds.  Built
+ * with log2(count) doubling steps of the jump-ahead matrices (one matrix
+ * application per stream).  Requires (count - 1) * 2^log2_spacing < 2^64,
+ * else XG_EINVAL; also XG_EINVAL for a stream range out of bounds or a
+ * running server.  Synchronous. */
+xg_status xg_seed_substreams(xg_ctx* ctx, uint32_t first, uint32_t count, uint32_t seed, uint32_t log2_spacing);
+
 /* ---- serving: continuous batching of requests --------------------------- */
 
 typedef struct {

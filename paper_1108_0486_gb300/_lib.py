@@ -109,6 +109,7 @@ SIGNATURES = {
     "xg_w64_set_launch": [vp, i32, u32, u32, u32],
     "xg_w64_autotune": [vp, i32, u32, u64, P_u32, P_u32, P_u32, ctypes.POINTER(ctypes.c_float)],
     "xg_w64_jump": [vp, u32, u32, u64],
+    "xg_seed_substreams": [vp, u32, u32, u32, u32],
 }
 _RESTYPES = {"xg_last_error": ctypes.c_char_p, "xg_version": ctypes.c_char_p}
 
@@ -249,6 +250,10 @@ def xg_set_batch_split(ctx, piece_words) -> None:
 
 def xg_jump(ctx, first, nstreams, words) -> None:
     call("xg_jump", ctypes.c_void_p(ctx), first, nstreams, words)
+
+
+def xg_seed_substreams(ctx, first, count, seed, log2_spacing) -> None:
+    call("xg_seed_substreams", ctypes.c_void_p(ctx), first, count, seed, log2_spacing)
 
 
 def xg_server_start(ctx, mem_cap_bytes=0, max_batch=0, lanes=0) -> None:

@@ -161,6 +161,12 @@ class Streams:
         count = self.n - first if count is None else count
         L.xg_jump(self.ctx, first, count, words)
 
+    def seed_substreams(self, seed: int, log2_spacing: int, first: int = 0, count=None):
+        """Streams first + i start at position i * 2^log2_spacing of the one
+        sequence seeded by `seed` (disjoint blocks of one period)."""
+        count = self.n - first if count is None else count
+        L.xg_seed_substreams(self.ctx, first, count, seed, log2_spacing)
+
     def serve(self, mem_cap_bytes: int = 0, max_batch: int = 0, lanes: int = 0) -> "Server":
         return Server(self, mem_cap_bytes, max_batch, lanes)
 

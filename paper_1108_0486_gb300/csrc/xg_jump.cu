@@ -186,6 +186,24 @@ __global__ void scatter_rings_kernel(State st, uint32_t first, uint32_t n, const
     }
 }
 
+// Substreams: stream first + m takes rings[m] (its ring after m * 2^q words
+// of the seeded sequence), the Weyl word w0 + m 2^q omega and position m 2^q.
+__global__ void substream_scatter_kernel(State st, uint32_t first, uint32_t n, const uint32_t* __restrict__ rings,
+                                         const uint32_t* __restrict__ w0, int q, uint32_t omega)
+{
+    const uint32_t m = blockIdx.x;
+    if (m >= n) return;
+    const uint32_t s = first + m;
+    uint32_t* dst = st.win + (size_t)s * kWin + kRingBase;
+    for (int w = threadIdx.x; w < kR; w += blockDim.x) dst[w] = rings[(size_t)m * kR + w];
+    if (threadIdx.x == 0) {
+        const uint64_t off = (uint64_t)m << q;
+        st.weyl[s] = *w0 + (uint32_t)off * omega;
+        st.pend[s] = 0;
+        st.pos[s] = off;
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -331,5 +349,70 @@ extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uin
     cudaFreeAsync(rings, s);
     cudaFreeAsync(ids, s);
     if (e != cudaSuccess) return cuda_fail(e, "xg_jump");
+    return XG_OK;
+}
+
+extern "C" xg_status xg_seed_substreams(xg_ctx* ctx, uint32_t first, uint32_t count, uint32_t seed,
+                                        uint32_t log2_spacing)
+{
+    using namespace xg;
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if ((uint64_t)first + count > ctx->n) return fail(XG_EINVAL, "streams out of range");
+    if (count == 0) return XG_OK;
+    if (ctx->server) return fail(XG_EINVAL, "the request server owns this context; stop it first");
+    // the last stream starts at (count - 1) * 2^q, which must fit in 64 bits
+    int steps = 0;   // doubling steps: bits of count - 1
+    while (steps < 32 && ((uint64_t)(count - 1) >> steps)) ++steps;
+    if (log2_spacing > 63 || (count > 1 && (int)log2_spacing + steps > 64))
+        return fail(XG_EINVAL, "(count - 1) * 2^%u does not fit in 64 bits", log2_spacing);
+    if (xg_status s = xg_seed(ctx, first, 1, &seed)) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t s = ctx->stream;
+    const int q = (int)log2_spacing;
+    xg_status st = XG_OK;
+    for (int b = 0; b < steps; ++b)
+        if (!jump_matrix(ctx->device, (int)ctx->param_set, q + b, s, &st)) return st;
+    // host lists: [first] | per step b, sources m - 2^b then destinations m,
+    // for m in [2^b, min(2^(b+1), count))
+    std::vector<uint32_t> h(1 + 2 * (size_t)(count - 1));
+    h[0] = first;
+    std::vector<size_t> src_off(steps), dst_off(steps);
+    std::vector<uint32_t> cnt(steps);
+    size_t o = 1;
+    for (int b = 0; b < steps; ++b) {
+        const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, count);
+        cnt[b] = hi - lo;
+        src_off[b] = o;
+        for (uint32_t m = lo; m < hi; ++m) h[o++] = m - lo;
+        dst_off[b] = o;
+        for (uint32_t m = lo; m < hi; ++m) h[o++] = m;
+    }
+    uint32_t* rings = nullptr;
+    uint32_t* lists = nullptr;   // the host lists, then the gathered Weyl word
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)count * kR * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&lists), (h.size() + 1) * 4, s);
+    if (e != cudaSuccess) {
+        if (rings) cudaFreeAsync(rings, s);
+        return cuda_fail(e, "xg_seed_substreams scratch");
+    }
+    uint32_t* d_w0 = lists + h.size();
+    e = cudaMemcpyAsync(lists, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_gather_rings(ctx->st, lists, 1, rings, nullptr, d_w0, 1, 0u, s);
+    for (int b = 0; b < steps && e == cudaSuccess; ++b) {
+        const uint64_t* C = jump_matrix(ctx->device, (int)ctx->param_set, q + b, s, &st);
+        e = zero_rings(rings, lists + dst_off[b], cnt[b], s);
+        if (e == cudaSuccess)
+            e = launch_gf2_apply_pairs(C, rings, cnt[b], lists + src_off[b], lists + dst_off[b], ctx->sm_count, s);
+    }
+    if (e == cudaSuccess) {
+        substream_scatter_kernel<<<count, 128, 0, s>>>(ctx->st, first, count, rings, d_w0, q,
+                                                       ctx->weyl_on ? 0x9E3779B9u : 0u);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
+    cudaFreeAsync(rings, s);
+    cudaFreeAsync(lists, s);
+    if (e != cudaSuccess) return cuda_fail(e, "xg_seed_substreams");
     return XG_OK;
 }

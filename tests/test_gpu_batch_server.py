@@ -368,6 +368,52 @@ def test_jump_composes_for_large_distances():
         assert torch.equal(x.normal(301), y.normal(301))
 
 
+@pytest.mark.parametrize("ps,q,count", [(0, 6, 37), (1, 6, 37), (0, 10, 100), (0, 0, 9)])
+def test_substreams_are_consecutive_blocks_of_one_sequence(ps, q, count):
+    """Stream i of seed_substreams starts at word i 2^q of the one seeded
+    sequence (the oracle run serially): with 2^q-word blocks, the streams'
+    outputs laid end to end are that sequence; positions are i 2^q."""
+    seed = 0x12345678
+    with Streams(count + 3, param_set=ps, seeds=W.seeds(count + 3)) as st:
+        st.seed_substreams(seed, q, first=2, count=count)
+        pos = st.checkpoint(first=2, count=count)["pos"]
+        got = st.u32(1 << q, first=2, count=count).cpu().numpy().view(np.uint32)
+        other = st.u32(5, first=0, count=2).cpu().numpy().view(np.uint32)
+    ref = O.Xorgens.param_set(ps).seed(seed).u32(count << q)
+    assert np.array_equal(got.reshape(-1), ref)
+    assert np.array_equal(pos, np.arange(count, dtype=np.uint64) << np.uint64(q))
+    # the streams outside the range keep their own seeds
+    assert np.array_equal(other, O.streams(W.seeds(count + 3)[:2], 5, param_set=ps))
+
+
+@pytest.mark.parametrize("q", [30, 40])
+def test_substreams_far_apart_equal_jumps(q):
+    """At 2^q-word spacing stream i equals the seeded stream jumped by i 2^q,
+    Weyl word included (2^30 omega is not 0 mod 2^32; normals use every bit)."""
+    seed = 99
+    with Streams(5) as a, Streams(5, seeds=[seed] * 5) as b:
+        a.seed_substreams(seed, q)
+        for i in range(1, 5):
+            b.jump(i << q, first=i, count=1)
+        assert torch.equal(a.normal(333), b.normal(333))
+        assert np.array_equal(a.checkpoint()["weyl"], b.checkpoint()["weyl"])
+
+
+def test_substreams_weyl_off_and_errors():
+    from paper_1108_0486_gb300 import XGError, _lib as L
+    with Streams(8, weyl=False) as st:
+        st.seed_substreams(5, 7)
+        got = st.u32(128).cpu().numpy().view(np.uint32)
+        with pytest.raises(XGError) as e:      # 2 * 2^63 does not fit in 64 bits
+            st.seed_substreams(5, 63, count=3)
+        assert e.value.status == L.XG_EINVAL
+        with pytest.raises(XGError):
+            st.seed_substreams(5, 4, first=6, count=3)   # out of range
+        st.seed_substreams(5, 63, count=2)           # 1 * 2^63 fits
+    ref = O.Xorgens.param_set(0, weyl=False).seed(5).u32(8 * 128)
+    assert np.array_equal(got.reshape(-1), ref)
+
+
 @pytest.mark.parametrize("piece", [64, 1024])
 def test_batch_cut_into_pieces_equals_uncut(piece):
     rng = np.random.default_rng(31)
