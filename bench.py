@@ -413,6 +413,12 @@ def extra_rows(st, stream, torch, peak, sm_mhz=None):
     ms = _time(lambda: st.jump(J), stream, torch)
     rows["jump_16384_streams"] = {"words": J, "set_bits": bin(J).count("1"), "ms": ms,
                                   "us_per_stream_application": ms * 1e3 / (STREAMS * bin(J).count("1"))}
+    # 16384 disjoint substreams of one sequence, 2^40 words apart (14 doubling
+    # steps, one matrix application per stream); the streams are re-seeded
+    # with their own seeds afterwards
+    ms = _time(lambda: st.seed_substreams(1, 40), stream, torch)
+    rows["seed_substreams_16384_streams"] = {"log2_spacing": 40, "ms": ms}
+    st.seed(W.seeds(STREAMS))
     # one stream, 2^20 words (seed 0x12345678): latency of a single long call
     from paper_1108_0486_gb300 import Streams
     one = Streams(1, seeds=[W.SINGLE_STREAM["seed"]], stream=stream)
