@@ -106,6 +106,14 @@ xg_status xg_w64_autotune(xg_w64_ctx* ctx, xg_w64_type type, uint32_t nstreams, 
  * a stream range out of bounds, XG_ENOMEM / XG_ECUDA from the device. */
 xg_status xg_w64_jump(xg_w64_ctx* ctx, uint32_t first, uint32_t nstreams, uint64_t words);
 
+/* Seed streams [first, first+count) as consecutive, disjoint blocks of one
+ * sequence: stream first + i starts at position i * 2^log2_spacing of the
+ * sequence that xg_w64_seed gives for `seed` (as xg_seed_substreams does for
+ * the 32-bit generators).  Requires (count - 1) * 2^log2_spacing < 2^64, else
+ * XG_EINVAL; also XG_EINVAL for a stream range out of bounds.  Synchronous. */
+xg_status xg_w64_seed_substreams(xg_w64_ctx* ctx, uint32_t first, uint32_t count, uint32_t seed,
+                                 uint32_t log2_spacing);
+
 #ifdef __cplusplus
 }
 #endif

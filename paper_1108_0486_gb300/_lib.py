@@ -110,6 +110,7 @@ SIGNATURES = {
     "xg_w64_autotune": [vp, i32, u32, u64, P_u32, P_u32, P_u32, ctypes.POINTER(ctypes.c_float)],
     "xg_w64_jump": [vp, u32, u32, u64],
     "xg_seed_substreams": [vp, u32, u32, u32, u32],
+    "xg_w64_seed_substreams": [vp, u32, u32, u32, u32],
 }
 _RESTYPES = {"xg_last_error": ctypes.c_char_p, "xg_version": ctypes.c_char_p}
 
@@ -427,6 +428,10 @@ def xg_w64_set_launch(ctx, out_type, tpg, wpl, block=0) -> None:
 
 def xg_w64_jump(ctx, first, nstreams, words) -> None:
     call("xg_w64_jump", ctypes.c_void_p(ctx), first, nstreams, words)
+
+
+def xg_w64_seed_substreams(ctx, first, count, seed, log2_spacing) -> None:
+    call("xg_w64_seed_substreams", ctypes.c_void_p(ctx), first, count, seed, log2_spacing)
 
 
 def xg_w64_autotune(ctx, out_type, nstreams, n_per_stream):

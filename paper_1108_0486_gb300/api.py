@@ -354,6 +354,12 @@ class Streams64:
         count = self.n - first if count is None else count
         L.xg_w64_jump(self.ctx, first, count, words)
 
+    def seed_substreams(self, seed: int, log2_spacing: int, first: int = 0, count=None):
+        """Streams first + i start at position i * 2^log2_spacing of the one
+        sequence seeded by `seed`."""
+        count = self.n - first if count is None else count
+        L.xg_w64_seed_substreams(self.ctx, first, count, seed, log2_spacing)
+
     def _gen(self, fn, dtype, n, first, count, out, ld):
         count = self.n - first if count is None else count
         if out is None:

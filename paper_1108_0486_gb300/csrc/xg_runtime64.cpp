@@ -323,6 +323,65 @@ xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t
     return XG_OK;
 }
 
+xg_status xg_w64_seed_substreams(xg_w64_ctx* c, uint32_t first, uint32_t count, uint32_t seed,
+                                 uint32_t log2_spacing)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if ((uint64_t)first + count > c->n) return fail(XG_EINVAL, "streams out of range");
+    if (count == 0) return XG_OK;
+    int steps = 0;   // doubling steps: bits of count - 1
+    while (steps < 32 && ((uint64_t)(count - 1) >> steps)) ++steps;
+    if (log2_spacing > 63 || (count > 1 && (int)log2_spacing + steps > 64))
+        return fail(XG_EINVAL, "(count - 1) * 2^%u does not fit in 64 bits", log2_spacing);
+    if (xg_status s = xg_w64_seed(c, first, 1, &seed)) return s;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t s = c->stream;
+    const int q = (int)log2_spacing;
+    xg_status st = XG_OK;
+    for (int b = 0; b < steps; ++b)
+        if (!xg::jump_matrix(c->device, xg::kJumpSetW64, q + b, s, &st)) return st;
+    // per step b: sources m - 2^b, then destinations m, m in [2^b, min(2^(b+1), count))
+    std::vector<uint32_t> h(2 * (size_t)(count - 1) + 1);
+    std::vector<size_t> src_off(steps), dst_off(steps);
+    std::vector<uint32_t> cnt(steps);
+    size_t o = 0;
+    for (int b = 0; b < steps; ++b) {
+        const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, count);
+        cnt[b] = hi - lo;
+        src_off[b] = o;
+        for (uint32_t m = lo; m < hi; ++m) h[o++] = m - lo;
+        dst_off[b] = o;
+        for (uint32_t m = lo; m < hi; ++m) h[o++] = m;
+    }
+    uint64_t* rings = nullptr;
+    uint32_t* lists = nullptr;   // the pair lists, then (8-byte aligned) the base Weyl word
+    const size_t w0_off = (h.size() * 4 + 7) / 8 * 8;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)count * xg64::kR * 8, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&lists), w0_off + 8, s);
+    if (e != cudaSuccess) {
+        if (rings) cudaFreeAsync(rings, s);
+        return cuda_fail(e, "xg_w64_seed_substreams scratch");
+    }
+    uint64_t* d_w0 = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(lists) + w0_off);
+    uint32_t* rings32 = reinterpret_cast<uint32_t*>(rings);
+    e = cudaMemcpyAsync(lists, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_w0, c->st.weyl + first, 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = xg64::launch_gather_rings(c->st, first, 1, rings, s);
+    for (int b = 0; b < steps && e == cudaSuccess; ++b) {
+        const uint64_t* C = xg::jump_matrix(c->device, xg::kJumpSetW64, q + b, s, &st);
+        e = xg::zero_rings(rings32, lists + dst_off[b], cnt[b], s);
+        if (e == cudaSuccess)
+            e = xg::launch_gf2_apply_pairs(C, rings32, cnt[b], lists + src_off[b], lists + dst_off[b], c->sm_count, s);
+    }
+    if (e == cudaSuccess)
+        e = xg64::launch_substream_scatter(c->st, first, count, rings, d_w0, q, c->weyl_on ? xg64::kOmega : 0, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
+    cudaFreeAsync(rings, s);
+    cudaFreeAsync(lists, s);
+    if (e != cudaSuccess) return cuda_fail(e, "xg_w64_seed_substreams");
+    return XG_OK;
+}
+
 xg_status xg_w64_transform_uniform_f64(xg_w64_ctx* c, const uint64_t* d_words, uint64_t n, double* d_out)
 {
     if (!c) return fail(XG_EINVAL, "null context");

@@ -436,6 +436,31 @@ __global__ void __launch_bounds__(64) scatter_rings_kernel(State st, uint32_t fi
     }
 }
 
+__global__ void __launch_bounds__(64) substream_scatter_kernel(State st, uint32_t first, uint32_t n,
+                                                               const uint64_t* __restrict__ rings,
+                                                               const uint64_t* __restrict__ w0, int q,
+                                                               uint64_t omega)
+{
+    const uint32_t m = blockIdx.x;
+    if (m >= n) return;
+    const uint32_t s = first + m;
+    st.win[(size_t)s * kWin + kRingBase + threadIdx.x] = rings[(size_t)m * kR + threadIdx.x];
+    if (threadIdx.x == 0) {
+        const uint64_t off = (uint64_t)m << q;
+        st.weyl[s] = *w0 + off * omega;
+        st.pend[s] = 0;
+        st.pos[s] = off;
+    }
+}
+
+cudaError_t launch_substream_scatter(const State& st, uint32_t first, uint32_t n, const uint64_t* rings,
+                                     const uint64_t* w0, int q, uint64_t omega, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    substream_scatter_kernel<<<n, kR, 0, s>>>(st, first, n, rings, w0, q, omega);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_rings(const State& st, uint32_t first, uint32_t n, uint64_t* rings, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;

@@ -69,5 +69,9 @@ cudaError_t launch_gather_rings(const State& st, uint32_t first, uint32_t n, uin
 // advanced by jump * omega and its position by jump.
 cudaError_t launch_scatter_rings(const State& st, uint32_t first, uint32_t n, const uint64_t* rings, uint64_t jump,
                                  uint64_t omega, cudaStream_t s);
+// Substreams: stream first + m takes rings[m] (pend = 0), the Weyl word
+// *w0 advanced by m 2^q omega, and position m 2^q.
+cudaError_t launch_substream_scatter(const State& st, uint32_t first, uint32_t n, const uint64_t* rings,
+                                     const uint64_t* w0, int q, uint64_t omega, cudaStream_t s);
 
 }  // namespace xg64

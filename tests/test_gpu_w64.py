@@ -189,3 +189,30 @@ def test_jump_composes_at_large_distances(api):
         x.jump(b)
         y.jump(a + b)
         assert np.array_equal(_u(x.u64(300)), _u(y.u64(300)))
+
+
+@pytest.mark.parametrize("q,count", [(5, 37), (0, 9), (12, 20)])
+def test_substreams_are_consecutive_blocks(api, q, count):
+    """Stream i of seed_substreams starts at word i 2^q of the one sequence
+    of the seed (the oracle run serially)."""
+    seed = 0x0BADF00D
+    st = api.Streams64(count + 2, seeds=list(range(1, count + 3)))
+    st.seed_substreams(seed, q, first=1, count=count)
+    got = _u(st.u64(1 << q, first=1, count=count))
+    ref = O.streams64([seed], count << q)[0]
+    assert np.array_equal(got.reshape(-1), ref)
+    # the neighbours keep their own seeds
+    assert np.array_equal(_u(st.u64(3, first=0, count=1))[0], O.streams64([1], 3)[0])
+
+
+def test_substreams_far_apart_equal_jumps(api):
+    seed = 4242
+    a = api.Streams64(4)
+    b = api.Streams64(4, seeds=[seed] * 4)
+    a.seed_substreams(seed, 37)
+    for i in range(1, 4):
+        b.jump(i << 37, first=i, count=1)
+    assert np.array_equal(_u(a.u64(200)), _u(b.u64(200)))
+    from paper_1108_0486_gb300 import _lib as L
+    with pytest.raises(L.XGError):
+        a.seed_substreams(seed, 63, count=3)
