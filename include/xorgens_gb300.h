@@ -53,7 +53,8 @@ typedef enum {
     XG_ETIMEDOUT = 4,  /* a bounded wait gave up */
     XG_ECUDA = 5,      /* a CUDA runtime call failed (message has the CUDA error) */
     XG_ENOTFOUND = 6,  /* unknown ticket */
-    XG_EDEVICE = 7     /* a kernel reported an internal error through its status word */
+    XG_EDEVICE = 7,    /* a kernel reported an internal error through its status word */
+    XG_ECANCELED = 8   /* the request was cancelled (xg_cancel) before it ran */
 } xg_status;
 
 typedef enum {
@@ -312,8 +313,17 @@ xg_status xg_poll(xg_ctx* ctx, uint64_t ticket, int* done, void** d_result);
 /* Poll until done or timeout_ms elapses (XG_ETIMEDOUT). */
 xg_status xg_wait(xg_ctx* ctx, uint64_t ticket, uint32_t timeout_ms, void** d_result);
 
-/* Forget a finished ticket and return its bytes (and pool buffer) to the cap. */
+/* Forget a finished (or cancelled) ticket and return its bytes (and pool
+ * buffer) to the cap. */
 xg_status xg_release(xg_ctx* ctx, uint64_t ticket);
+
+/* Cancel a request that has not been launched yet: it will never run, its
+ * stream does not advance for it (the stream's later requests read the words
+ * it would have read), and xg_poll / xg_wait report XG_ECANCELED for it from
+ * now on (xg_collect too, once the scheduler has dropped it); release it as
+ * any other ticket.  XG_EINVAL if the request is already on the GPU or
+ * finished (it then completes normally), XG_ENOTFOUND for an unknown ticket. */
+xg_status xg_cancel(xg_ctx* ctx, uint64_t ticket);
 
 /* Server clock timestamps of a ticket: submission, batch launch, completion
  * as seen by the host (0 while pending). */
@@ -325,7 +335,8 @@ xg_status xg_server_stats_get(xg_ctx* ctx, xg_server_stats* out);
 typedef struct {
     uint64_t ticket;
     uint64_t t_submit_ns, t_launch_ns, t_done_ns; /* server clock */
-    int32_t status;                               /* XG_OK, or XG_EDEVICE if its batch failed */
+    int32_t status;                               /* XG_OK, XG_EDEVICE if its batch failed,
+                                                     XG_ECANCELED if it was cancelled */
     uint32_t pad;
     void* d_result;                               /* output pointer (NULL once released) */
 } xg_completion;

@@ -13,10 +13,10 @@ import threading
 
 from .build import LIB_PATH
 
-XG_OK, XG_EINVAL, XG_ENOMEM, XG_EAGAIN, XG_ETIMEDOUT, XG_ECUDA, XG_ENOTFOUND, XG_EDEVICE = range(8)
+XG_OK, XG_EINVAL, XG_ENOMEM, XG_EAGAIN, XG_ETIMEDOUT, XG_ECUDA, XG_ENOTFOUND, XG_EDEVICE, XG_ECANCELED = range(9)
 XG_U32, XG_UNIFORM_F32, XG_NORMAL_F32 = 0, 1, 2
 STATUS_NAMES = {0: "XG_OK", 1: "XG_EINVAL", 2: "XG_ENOMEM", 3: "XG_EAGAIN", 4: "XG_ETIMEDOUT",
-                5: "XG_ECUDA", 6: "XG_ENOTFOUND", 7: "XG_EDEVICE"}
+                5: "XG_ECUDA", 6: "XG_ENOTFOUND", 7: "XG_EDEVICE", 8: "XG_ECANCELED"}
 
 
 class XGError(RuntimeError):
@@ -87,6 +87,7 @@ SIGNATURES = {
     "xg_poll": [vp, u64, P_i32, P_vp],
     "xg_wait": [vp, u64, u32, P_vp],
     "xg_release": [vp, u64],
+    "xg_cancel": [vp, u64],
     "xg_ticket_times": [vp, u64, P_u64, P_u64, P_u64],
     "xg_server_stats_get": [vp, vp],
     "xg_collect": [vp, vp, u32, P_u32, i32],
@@ -311,6 +312,10 @@ def xg_wait(ctx, ticket, timeout_ms=10000):
 
 def xg_release(ctx, ticket) -> None:
     call("xg_release", ctypes.c_void_p(ctx), ticket)
+
+
+def xg_cancel(ctx, ticket) -> None:
+    call("xg_cancel", ctypes.c_void_p(ctx), ticket)
 
 
 def xg_ticket_times(ctx, ticket):

@@ -206,6 +206,10 @@ class Server:
     def release(self, ticket: int):
         L.xg_release(self.ctx, ticket)
 
+    def cancel(self, ticket: int):
+        """Cancel a request not yet launched (XGError XG_EINVAL if it is)."""
+        L.xg_cancel(self.ctx, ticket)
+
     def times(self, ticket: int):
         return L.xg_ticket_times(self.ctx, ticket)
 

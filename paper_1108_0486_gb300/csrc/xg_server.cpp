@@ -221,7 +221,10 @@ struct Ticket {
     size_t bytes = 0;
     uint32_t slot = 0;
     uint32_t expected = 1;      // completion increments: 1, or the pieces it was cut into
-    std::atomic<int> state{0};  // kQueued, kRunning, kDone, kFailed
+    std::atomic<int> state{0};  // kQueued, kRunning, kDone, kFailed, kCancelled
+    // who owns a queued request: 0 = nobody yet, 1 = the scheduler took it
+    // into a batch, 2 = xg_cancel took it (the one that swaps it from 0 wins)
+    std::atomic<int> claim{0};
     uint64_t t_submit = 0, t_launch = 0;
     std::atomic<uint64_t> t_done{0};
     std::shared_ptr<Ticket> next_in_stream;  // the stream's queue (scheduler thread only)
@@ -249,7 +252,8 @@ struct StreamQueue {
     }
 };
 
-enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
+enum { kUnclaimed = 0, kClaimedByBatch = 1, kClaimedByCancel = 2 };
 
 class Server {
 public:
@@ -444,7 +448,7 @@ public:
     bool check_flag(Ticket& t)
     {
         const int st = t.state.load(std::memory_order_acquire);
-        if (st == kDone || st == kFailed) return true;
+        if (st == kDone || st == kFailed || st == kCancelled) return true;
         if (t.state.load(std::memory_order_acquire) != kRunning) return false;
         volatile uint32_t* f = h_flags_ + t.slot;
         if (*f < t.expected) return false;
@@ -460,6 +464,8 @@ public:
         const bool d = check_flag(*t);
         if (t->state.load() == kFailed) return fail(XG_EDEVICE, "ticket %llu failed: its batch did not run",
                                                     (unsigned long long)id);
+        if (t->state.load() == kCancelled)
+            return fail(XG_ECANCELED, "ticket %llu was cancelled", (unsigned long long)id);
         if (done) *done = d ? 1 : 0;
         if (out) *out = d ? t->out : nullptr;
         return XG_OK;
@@ -477,7 +483,22 @@ public:
         }
         if (t->state.load() == kFailed) return fail(XG_EDEVICE, "ticket %llu failed: its batch did not run",
                                                     (unsigned long long)id);
+        if (t->state.load() == kCancelled)
+            return fail(XG_ECANCELED, "ticket %llu was cancelled", (unsigned long long)id);
         if (out) *out = t->out;
+        return XG_OK;
+    }
+
+    xg_status cancel(uint64_t id)
+    {
+        auto t = find(id);
+        if (!t) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
+        int expect = kUnclaimed;
+        if (!t->claim.compare_exchange_strong(expect, kClaimedByCancel))
+            return fail(XG_EINVAL, "ticket %llu is already launched or cancelled", (unsigned long long)id);
+        // the scheduler drops it from its stream's queue when it reaches it
+        t->state.store(kCancelled, std::memory_order_release);
+        t->t_done.store(now_ns());
         return XG_OK;
     }
 
@@ -487,7 +508,7 @@ public:
         auto it = tickets_.find(id);
         if (it == tickets_.end()) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
         Ticket& t = *it->second;
-        if (t.state.load() != kDone && t.state.load() != kFailed) {
+        if (t.state.load() != kDone && t.state.load() != kFailed && t.state.load() != kCancelled) {
             // the scheduler may not have seen the flag yet
             volatile uint32_t* f = h_flags_ + t.slot;
             if (!(t.state.load() == kRunning && *f >= t.expected))
@@ -533,7 +554,8 @@ public:
             c.t_submit_ns = t->t_submit;
             c.t_launch_ns = t->t_launch;
             c.t_done_ns = t->t_done.load();
-            c.status = t->state.load() == kDone ? XG_OK : XG_EDEVICE;
+            const int tst = t->state.load();
+            c.status = tst == kDone ? XG_OK : tst == kCancelled ? XG_ECANCELED : XG_EDEVICE;
             c.pad = 0;
             c.d_result = t->out;
             if (release) {
@@ -685,6 +707,15 @@ private:
                     ready_.pop();
                     StreamQueue& q = queues_[s];
                     auto t = q.pop();
+                    int expect = kUnclaimed;
+                    if (!t->claim.compare_exchange_strong(expect, kClaimedByBatch)) {
+                        // cancelled: never runs; the stream's next request is ready
+                        --queued_;
+                        if (q.head) ready_.push({q.head->seq, s});
+                        std::lock_guard<std::mutex> dl(done_mu_);
+                        done_q_.push_back(std::move(t));
+                        continue;
+                    }
                     q.busy = true;
                     t->slot = (uint32_t)(li * cfg_.max_batch + items.size());
                     t->t_launch = t_launch;
@@ -891,6 +922,13 @@ xg_status xg_wait(xg_ctx* ctx, uint64_t ticket, uint32_t timeout_ms, void** d_re
     if (!ctx) return fail(XG_EINVAL, "null context");
     if (!ctx->server) return fail(XG_EINVAL, "server not running");
     return ctx->server->wait(ticket, timeout_ms, d_result);
+}
+
+xg_status xg_cancel(xg_ctx* ctx, uint64_t ticket)
+{
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if (!ctx->server) return fail(XG_EINVAL, "server not running");
+    return ctx->server->cancel(ticket);
 }
 
 xg_status xg_release(xg_ctx* ctx, uint64_t ticket)

@@ -620,3 +620,51 @@ def test_contexts_on_concurrent_cuda_streams():
     refs = oracle_per_item(W.seeds(8, start=77), [(i, KINDS[i % 3], 200000 + i) for i in range(8)])
     for i in range(8):
         check(KINDS[i % 3], outs_c[i][:200000 + i], refs[i])
+
+
+def test_server_cancel_queued_requests():
+    """Requests queued behind a long one on the same stream can be
+    cancelled: they never run, the stream's later requests read the words
+    they would have read, poll/wait report XG_ECANCELED, xg_collect reports
+    them, and release returns their bytes.  A finished request cannot be
+    cancelled."""
+    from paper_1108_0486_gb300 import XGError, _lib as L
+    seeds = W.seeds(2, start=500)
+    sizes = [1 << 25, 5000, 6000, 7000, 8000, 9000]
+    with Streams(2, seeds=seeds) as st:
+        st.set_batch_split(1)   # no cutting: the first request is one warp's 20 ms
+        srv = st.serve(lanes=4)
+        tickets = [srv.submit(0, "u32", n) for n in sizes]
+        # the first request keeps stream 0 busy for far longer than this
+        srv.cancel(tickets[2])
+        srv.cancel(tickets[4])
+        with pytest.raises(XGError) as e:
+            srv.cancel(tickets[2])            # already cancelled
+        assert e.value.status == L.XG_EINVAL
+        kept = [0, 1, 3, 5]
+        outs = {i: srv.result(tickets[i], "u32", sizes[i], timeout_ms=60000).clone() for i in kept}
+        for i in (2, 4):
+            with pytest.raises(XGError) as e:
+                srv.wait(tickets[i])
+            assert e.value.status == L.XG_ECANCELED
+        with pytest.raises(XGError) as e:
+            srv.cancel(tickets[0])            # finished
+        assert e.value.status == L.XG_EINVAL
+        done = {}
+        for _ in range(200):
+            for (t, _, _, _, status, _) in srv.collect(64):
+                done[t] = status
+            if len(done) == len(sizes):
+                break
+            time.sleep(0.005)
+        assert {done[tickets[i]] for i in (2, 4)} == {L.XG_ECANCELED}
+        assert all(done[tickets[i]] == L.XG_OK for i in kept)
+        for t in tickets:
+            srv.release(t)
+        assert srv.stats()["outstanding_bytes"] == 0
+        srv.stop()
+    seq = O.Xorgens.param_set(0).seed(int(seeds[0])).u32(sum(sizes[i] for i in kept))
+    off = 0
+    for i in kept:
+        assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), seq[off:off + sizes[i]]), i
+        off += sizes[i]
