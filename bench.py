@@ -444,6 +444,14 @@ def extra_rows(st, stream, torch, peak, sm_mhz=None):
                                "hbm_frac": rn64 * 8 / (ms_f / 1e3) / 1e9 / peak, "launch": tuned64}
     rows["w64_u64"] = {"rn_s": rn64 / (ms_u / 1e3), "ms": ms_u,
                        "hbm_frac": rn64 * 8 / (ms_u / 1e3) / 1e9 / peak, "launch": tuned64u}
+    one64 = Streams64(1, seeds=[W.SINGLE_STREAM["seed"]], stream=stream)
+    o64 = torch.empty((1, nb), dtype=torch.int64, device="cuda")
+    ms_cut64 = _time(lambda: one64.u64(nb, out=o64), stream, torch)
+    one64.set_split(1)
+    ms_serial64 = _time(lambda: one64.u64(nb, out=o64), stream, torch)
+    one64.close()
+    rows["w64_single_stream_2p20_u64"] = {"ms": ms_cut64, "rn_s": nb / (ms_cut64 / 1e3),
+                                          "ms_one_warp_uncut": ms_serial64}
     ms_j = _time(lambda: s64.jump(J), stream, torch)
     rows["w64_jump_16384_streams"] = {"words": J, "set_bits": bin(J).count("1"), "ms": ms_j,
                                       "us_per_stream_application": ms_j * 1e3 / (STREAMS * bin(J).count("1"))}

@@ -96,6 +96,15 @@ xg_status xg_w64_set_launch(xg_w64_ctx* ctx, xg_w64_type type, uint32_t tpg, uin
 xg_status xg_w64_autotune(xg_w64_ctx* ctx, xg_w64_type type, uint32_t nstreams, uint64_t n_per_stream,
                           uint32_t* tpg, uint32_t* wpl, uint32_t* block, float* best_ms);
 
+/* Long calls on few streams (at most 16 streams, at least 2^18 words each,
+ * device output) are cut into pieces that run on many warps at once, each
+ * starting from the stream's state jumped ahead by its offset (xg_w64_jump's
+ * matrices); the output and the stream's final state are exactly those of
+ * the uncut call.  piece_words: 0 = automatic (about four pieces per SM
+ * sub-partition in all, at least 2^16 words), 1 = never cut, else a power of
+ * two >= 64.  XG_EINVAL for other values. */
+xg_status xg_w64_set_split(xg_w64_ctx* ctx, uint64_t piece_words);
+
 /* Jump-ahead: advance streams [first, first+nstreams) by `words` positions
  * without generating them, exactly as if that many words had been drawn.
  * The recurrence is linear over GF(2) on the 4096-bit ring (Sec. 2), so the

@@ -112,6 +112,7 @@ SIGNATURES = {
     "xg_w64_jump": [vp, u32, u32, u64],
     "xg_seed_substreams": [vp, u32, u32, u32, u32],
     "xg_w64_seed_substreams": [vp, u32, u32, u32, u32],
+    "xg_w64_set_split": [vp, u64],
 }
 _RESTYPES = {"xg_last_error": ctypes.c_char_p, "xg_version": ctypes.c_char_p}
 
@@ -433,6 +434,10 @@ def xg_w64_set_launch(ctx, out_type, tpg, wpl, block=0) -> None:
 
 def xg_w64_jump(ctx, first, nstreams, words) -> None:
     call("xg_w64_jump", ctypes.c_void_p(ctx), first, nstreams, words)
+
+
+def xg_w64_set_split(ctx, piece_words) -> None:
+    call("xg_w64_set_split", ctypes.c_void_p(ctx), piece_words)
 
 
 def xg_w64_seed_substreams(ctx, first, count, seed, log2_spacing) -> None:

@@ -364,6 +364,10 @@ class Streams64:
         count = self.n - first if count is None else count
         L.xg_w64_seed_substreams(self.ctx, first, count, seed, log2_spacing)
 
+    def set_split(self, piece_words: int):
+        """0: automatic, 1: never cut long calls on few streams, else the piece length."""
+        L.xg_w64_set_split(self.ctx, piece_words)
+
     def _gen(self, fn, dtype, n, first, count, out, ld):
         count = self.n - first if count is None else count
         if out is None:

@@ -29,6 +29,7 @@ struct xg_w64_ctx {
     int blk[2] = {0, 0};
     void* staging = nullptr;
     size_t staging_bytes = 0;
+    uint64_t split_words = 0;   // cut calls: 0 automatic, 1 never, else the piece length
     std::mutex mu;
 };
 
@@ -81,6 +82,103 @@ xg_status enqueue(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstreams, ui
     return e == cudaSuccess ? XG_OK : cuda_fail(e, "64-bit generate kernel launch");
 }
 
+// Few streams, long calls: one stream is one serial chain (one warp), so the
+// call is cut into K pieces of L = 2^q words per stream whose start states
+// come from the jump-ahead matrices (piece m = the stream advanced m L
+// words), generated as K streams of a scratch state, and the stream then
+// takes the state of its last piece.  The output is exactly the uncut call's.
+constexpr uint32_t kCutMaxStreams = 16;
+constexpr uint64_t kCutMinWords = uint64_t(1) << 18;
+
+xg_status generate_cut(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstreams, uint64_t n, void* d_out,
+                       uint64_t ld)
+{
+    // piece length: about four pieces per SM sub-partition in all, at least 2^16
+    int q = 16;
+    if (c->split_words > 1) {
+        while ((uint64_t(1) << q) < c->split_words) ++q;
+    } else {
+        const uint64_t target = std::max<uint64_t>(1, (uint64_t)c->sm_count * 4 / nstreams);
+        while (q < 40 && (uint64_t(1) << q) * target < n) ++q;
+    }
+    const uint64_t L = uint64_t(1) << q;
+    const uint64_t K64 = (n + L - 1) / L;
+    if (K64 < 2 || K64 * nstreams > (uint64_t(1) << 20)) return enqueue(c, kind, first, nstreams, n, d_out, ld);
+    const uint32_t K = (uint32_t)K64;
+    const uint32_t P = nstreams * K;
+    cudaStream_t s = c->stream;
+    int steps = 0;   // doubling steps: bits of K - 1
+    while (((uint64_t)(K - 1) >> steps)) ++steps;
+    xg_status st = XG_OK;
+    for (int b = 0; b < steps; ++b)
+        if (!xg::jump_matrix(c->device, xg::kJumpSetW64, q + b, s, &st)) return st;
+    // pair lists per step b: sources i K + m - 2^b, destinations i K + m
+    std::vector<uint32_t> h;
+    std::vector<size_t> src_off(steps), dst_off(steps);
+    std::vector<uint32_t> cnt(steps);
+    for (int b = 0; b < steps; ++b) {
+        const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, K);
+        cnt[b] = (hi - lo) * nstreams;
+        src_off[b] = h.size();
+        for (uint32_t i = 0; i < nstreams; ++i)
+            for (uint32_t m = lo; m < hi; ++m) h.push_back(i * K + m - lo);
+        dst_off[b] = h.size();
+        for (uint32_t i = 0; i < nstreams; ++i)
+            for (uint32_t m = lo; m < hi; ++m) h.push_back(i * K + m);
+    }
+    // scratch: rings[P][64] | piece state (window, Weyl, pend, pos) | lists
+    const size_t off_win = (size_t)P * xg64::kR * 8;
+    const size_t off_weyl = off_win + (size_t)P * xg64::kWin * 8;
+    const size_t off_pos = off_weyl + (size_t)P * 8;
+    const size_t off_pend = off_pos + (size_t)P * 8;
+    const size_t off_lists = align_up(off_pend + (size_t)P * 4, 16);
+    const size_t total = off_lists + h.size() * 4 + 4;
+    char* scratch = nullptr;
+    XG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, s), "cut scratch");
+    uint64_t* rings = reinterpret_cast<uint64_t*>(scratch);
+    uint32_t* rings32 = reinterpret_cast<uint32_t*>(scratch);
+    uint32_t* lists = reinterpret_cast<uint32_t*>(scratch + off_lists);
+    xg64::State pieces{reinterpret_cast<uint64_t*>(scratch + off_win), reinterpret_cast<uint64_t*>(scratch + off_weyl),
+                       reinterpret_cast<uint32_t*>(scratch + off_pend), reinterpret_cast<uint64_t*>(scratch + off_pos)};
+    cudaError_t e = cudaSuccess;
+    if (!h.empty()) e = cudaMemcpyAsync(lists, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
+    // piece 0 of each stream: the stream's own ring (gathered one stream at a time)
+    for (uint32_t i = 0; i < nstreams && e == cudaSuccess; ++i)
+        e = xg64::launch_gather_rings(c->st, first + i, 1, rings + (size_t)i * K * xg64::kR, s);
+    for (int b = 0; b < steps && e == cudaSuccess; ++b) {
+        const uint64_t* C = xg::jump_matrix(c->device, xg::kJumpSetW64, q + b, s, &st);
+        e = xg::zero_rings(rings32, lists + dst_off[b], cnt[b], s);
+        if (e == cudaSuccess)
+            e = xg::launch_gf2_apply_pairs(C, rings32, cnt[b], lists + src_off[b], lists + dst_off[b], c->sm_count, s);
+    }
+    const uint64_t omega = c->weyl_on ? xg64::kOmega : 0;
+    if (e == cudaSuccess) e = xg64::launch_init_pieces(c->st, first, nstreams, K, L, rings, pieces, omega, s);
+    xg_status gst = XG_OK;
+    if (e == cudaSuccess) {
+        // the full pieces of each stream as K - 1 streams with ld = L, then its last piece
+        xg_w64_ctx view = {};
+        view.sm_count = c->sm_count;
+        view.stream = s;
+        view.st = pieces;
+        view.weyl_on = c->weyl_on;
+        view.cfg[0] = c->cfg[0];
+        view.cfg[1] = c->cfg[1];
+        view.blk[0] = c->blk[0];
+        view.blk[1] = c->blk[1];
+        const uint64_t last = n - (uint64_t)(K - 1) * L;
+        for (uint32_t i = 0; i < nstreams && gst == XG_OK; ++i) {
+            char* row = static_cast<char*>(d_out) + (uint64_t)i * ld * 8;
+            gst = enqueue(&view, kind, i * K, K - 1, L, row, L);
+            if (gst == XG_OK) gst = enqueue(&view, kind, i * K + K - 1, 1, last, row + (uint64_t)(K - 1) * L * 8, last);
+        }
+        if (gst == XG_OK) e = xg64::launch_adopt_last_piece(c->st, first, nstreams, K, pieces, n, s);
+    }
+    cudaFreeAsync(scratch, s);
+    if (gst != XG_OK) return gst;
+    if (e != cudaSuccess) return cuda_fail(e, "64-bit cut generation");
+    return XG_OK;
+}
+
 // Host output: generate into one device buffer piece by piece and copy each
 // piece out (synchronously); pieces split the stream range and, for long
 // requests, each stream's length.
@@ -129,7 +227,11 @@ xg_status generate(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstreams, u
     if (ld > (UINT64_MAX / 16) / nstreams) return fail(XG_EINVAL, "output extent overflows");
     if (reinterpret_cast<uintptr_t>(out) & 7u) return fail(XG_EINVAL, "output must be 8-byte aligned");
     std::lock_guard<std::mutex> lk(c->mu);
-    if (is_device_pointer(out)) return enqueue(c, kind, first, nstreams, n, out, ld);
+    if (is_device_pointer(out)) {
+        if (nstreams <= kCutMaxStreams && n >= kCutMinWords && c->split_words != 1)
+            return generate_cut(c, kind, first, nstreams, n, out, ld);
+        return enqueue(c, kind, first, nstreams, n, out, ld);
+    }
     return to_host(c, kind, first, nstreams, n, out, ld);
 }
 
@@ -270,6 +372,15 @@ xg_status xg_w64_generate_uniform_f64(xg_w64_ctx* c, uint32_t first, uint32_t ns
                                       uint64_t ld)
 {
     return generate(c, xg64::kUniformF64, first, nstreams, n, out, ld);
+}
+
+xg_status xg_w64_set_split(xg_w64_ctx* c, uint64_t piece_words)
+{
+    if (!c) return fail(XG_EINVAL, "null context");
+    if (piece_words > 1 && (piece_words < 64 || (piece_words & (piece_words - 1))))
+        return fail(XG_EINVAL, "piece length must be 0, 1 or a power of two >= 64");
+    c->split_words = piece_words;
+    return XG_OK;
 }
 
 xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t words)

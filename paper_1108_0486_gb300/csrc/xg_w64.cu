@@ -461,6 +461,48 @@ cudaError_t launch_substream_scatter(const State& st, uint32_t first, uint32_t n
     return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(64) init_pieces_kernel(State real, uint32_t first, uint32_t K, uint64_t L,
+                                                         const uint64_t* __restrict__ rings, State pieces,
+                                                         uint64_t omega)
+{
+    const uint32_t p = blockIdx.x;   // piece p = i K + m
+    const uint32_t i = p / K, m = p % K;
+    pieces.win[(size_t)p * kWin + kRingBase + threadIdx.x] = rings[(size_t)p * kR + threadIdx.x];
+    if (threadIdx.x == 0) {
+        pieces.weyl[p] = real.weyl[first + i] + (uint64_t)m * L * omega;
+        pieces.pend[p] = 0;
+        pieces.pos[p] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(96) adopt_last_piece_kernel(State real, uint32_t first, uint32_t K, State pieces,
+                                                              uint64_t n)
+{
+    const uint32_t i = blockIdx.x;
+    const uint32_t p = i * K + (K - 1);
+    const uint32_t s = first + i;
+    real.win[(size_t)s * kWin + threadIdx.x] = pieces.win[(size_t)p * kWin + threadIdx.x];
+    if (threadIdx.x == 0) {
+        real.weyl[s] = pieces.weyl[p];
+        real.pend[s] = pieces.pend[p];
+        real.pos[s] += n;
+    }
+}
+
+cudaError_t launch_init_pieces(const State& real, uint32_t first, uint32_t nstreams, uint32_t K, uint64_t L,
+                               const uint64_t* rings, const State& pieces, uint64_t omega, cudaStream_t s)
+{
+    init_pieces_kernel<<<nstreams * K, kR, 0, s>>>(real, first, K, L, rings, pieces, omega);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adopt_last_piece(const State& real, uint32_t first, uint32_t nstreams, uint32_t K,
+                                    const State& pieces, uint64_t n, cudaStream_t s)
+{
+    adopt_last_piece_kernel<<<nstreams, kWin, 0, s>>>(real, first, K, pieces, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_rings(const State& st, uint32_t first, uint32_t n, uint64_t* rings, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;

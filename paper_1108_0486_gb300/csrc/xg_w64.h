@@ -74,4 +74,15 @@ cudaError_t launch_scatter_rings(const State& st, uint32_t first, uint32_t n, co
 cudaError_t launch_substream_scatter(const State& st, uint32_t first, uint32_t n, const uint64_t* rings,
                                      const uint64_t* w0, int q, uint64_t omega, cudaStream_t s);
 
+// Cut calls: a long call on stream first + i is generated as K pieces of L
+// words, piece m by stream i K + m of a scratch state `pieces` whose ring is
+// rings[i K + m] (the real ring advanced m L words) and whose Weyl word is
+// the real one advanced by m L omega.
+cudaError_t launch_init_pieces(const State& real, uint32_t first, uint32_t nstreams, uint32_t K, uint64_t L,
+                               const uint64_t* rings, const State& pieces, uint64_t omega, cudaStream_t s);
+// After the pieces ran: stream first + i takes the state of its last piece
+// (window, Weyl word, pending words) and its position advances by n.
+cudaError_t launch_adopt_last_piece(const State& real, uint32_t first, uint32_t nstreams, uint32_t K,
+                                    const State& pieces, uint64_t n, cudaStream_t s);
+
 }  // namespace xg64

@@ -216,3 +216,33 @@ def test_substreams_far_apart_equal_jumps(api):
     from paper_1108_0486_gb300 import _lib as L
     with pytest.raises(L.XGError):
         a.seed_substreams(seed, 63, count=3)
+
+
+@pytest.mark.parametrize("split", [0, 1 << 10])
+def test_long_calls_on_few_streams_are_cut_exactly(api, split):
+    """Calls of 2^18 words and more on few streams run as jump-ahead pieces;
+    outputs and the states left behind equal the serial stream's."""
+    seeds = [5, 6, 7]
+    n = (1 << 18) + 12345
+    st = api.Streams64(3, seeds=seeds)
+    st.set_split(split)
+    out = torch.empty((3, n + 3), dtype=torch.int64, device="cuda")   # ld > n
+    st.u64(n, out=out[:, :n], ld=n + 3)
+    f = st.uniform(n)
+    tail = _u(st.u64(1000))
+    ref = O.streams64(seeds, 2 * n + 1000)
+    assert np.array_equal(_u(out[:, :n]), ref[:, :n])
+    assert np.array_equal(f.cpu().numpy(), O.uniform64_of(ref[:, n:2 * n]).reshape(3, n))
+    assert np.array_equal(tail, ref[:, 2 * n:])
+
+
+def test_long_single_stream_cut_and_uncut_agree(api):
+    a = api.Streams64(1, seeds=[77])
+    b = api.Streams64(1, seeds=[77])
+    b.set_split(1)
+    n = 1 << 20
+    assert np.array_equal(_u(a.u64(n)), _u(b.u64(n)))
+    assert np.array_equal(_u(a.u64(333)), _u(b.u64(333)))
+    from paper_1108_0486_gb300 import _lib as L
+    with pytest.raises(L.XGError):
+        a.set_split(100)   # not a power of two
