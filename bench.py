@@ -805,6 +805,10 @@ def profile_kernel(args):
             out["launch"] = st.autotune("uniform", n)
         buf = torch.empty((STREAMS, n), dtype=torch.float64, device="cuda")
         out["ms"] = _time(lambda: st.uniform(n, out=buf), stream, torch, reps=args.steps, warm=args.warmup)
+    elif args.kernel == "jump":
+        # one matrix application per stream per call (2^20 has one set bit)
+        st = Streams(STREAMS, seeds=W.seeds(STREAMS), stream=stream)
+        out["ms"] = _time(lambda: st.jump(1 << 20), stream, torch, reps=args.steps, warm=args.warmup)
     elif args.kernel == "batch":
         items = [it for it in W.batched_uneven() if it.count <= n] if args.n_per else W.batched_uneven()
         st = Streams(4096, seeds=W.seeds(4096), stream=stream)
@@ -828,7 +832,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="arrival window of the serving row (10 s for the full 200K requests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["u32", "uniform", "normal", "normal_sum", "batch", "w64_uniform"],
+    ap.add_argument("--kernel", default=None, choices=["u32", "uniform", "normal", "normal_sum", "batch", "w64_uniform", "jump"],
                     help="time one kernel's workload alone (profiling case; not a bench line)")
     ap.add_argument("--n-per", type=int, default=None,
                     help="override words per stream (profiling of a smaller case; not a bench line)")
