@@ -397,6 +397,15 @@ def test_argument_errors():
             L.xg_generate_u32(st.ctx, 0, 10, 100, 0, 100)               # null
         with pytest.raises(XGError):
             st.set_launch("u32", 8, 8)                                    # unsupported
+        words = torch.zeros(64, dtype=torch.int32, device="cuda")
+        res = torch.empty(64, dtype=torch.float32, device="cuda")
+        with pytest.raises(XGError) as e:
+            L.xg_transform_normal(st.ctx, words.data_ptr(), 63, res.data_ptr())   # odd count
+        assert e.value.status == L.XG_EINVAL
+        with pytest.raises(XGError):
+            L.xg_transform_normal(st.ctx, words.data_ptr() + 4, 32, res.data_ptr())  # not 8-byte aligned
+        with pytest.raises(XGError):
+            L.xg_transform_uniform(st.ctx, words.data_ptr() + 2, 16, res.data_ptr())  # not 4-byte aligned
         # zero-size calls are no-ops and do not advance the streams
         L.xg_generate_u32(st.ctx, 0, 10, 0, out.data_ptr(), 100)
         L.xg_generate_u32(st.ctx, 0, 0, 100, out.data_ptr(), 100)
