@@ -683,9 +683,10 @@ def serving_bulk(torch, L, stream, rate, seconds, lanes=48, max_batch=1024, spli
     stats = L.xg_server_stats_get(st.ctx)
     L.xg_server_stop(st.ctx)
     st.close()
-    # tickets are issued in submission order from the first ticket number
-    base = int(tickets.min())
-    order = (tick_done - base).astype(np.int64)
+    # ticket numbers grow in submission order: each completion's request
+    # index is its ticket's rank
+    order = np.searchsorted(tickets, tick_done)
+    assert np.array_equal(tickets[order], tick_done)
     t_done = np.empty(n, dtype=np.float64)
     t_done[order] = done.astype(np.float64)
     lat_ms = (t_done - (t0 + arrival * 1e9)) / 1e6

@@ -290,7 +290,8 @@ xg_status xg_server_start(xg_ctx* ctx, const xg_server_config* cfg);
  * (pool results become invalid). */
 xg_status xg_server_stop(xg_ctx* ctx);
 
-/* Non-blocking.  XG_EAGAIN when admitting the request would put the
+/* Non-blocking.  Ticket numbers are nonzero and grow in submission order
+ * (not consecutively).  XG_EAGAIN when admitting the request would put the
  * outstanding output bytes above the cap (retry later, after xg_release);
  * XG_EINVAL for a request larger than the cap itself, which could never be
  * admitted. */

@@ -27,7 +27,6 @@
 #include <queue>
 #include <string>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "xg_batch.h"
@@ -252,6 +251,52 @@ struct StreamQueue {
     }
 };
 
+// Live tickets by id in O(1) without hashing: an id is
+// (submission sequence << kSlotBits) | slot, so ids grow in submission order
+// and the slot is read off the id (its ticket must carry the same id).
+class TicketTable {
+public:
+    static constexpr int kSlotBits = 24;
+    static constexpr uint64_t kSlotMask = (uint64_t(1) << kSlotBits) - 1;
+    void reserve(size_t n) { slots_.reserve(n); }
+    // Gives t the id of sequence number seq and a free slot; false when all
+    // 2^24 slots hold live tickets.
+    bool insert(const std::shared_ptr<Ticket>& t, uint64_t seq)
+    {
+        uint32_t slot;
+        if (!free_.empty()) {
+            slot = free_.back();
+            free_.pop_back();
+        } else {
+            if (slots_.size() > kSlotMask) return false;
+            slot = (uint32_t)slots_.size();
+            slots_.emplace_back();
+        }
+        t->id = (seq << kSlotBits) | slot;
+        slots_[slot] = t;
+        return true;
+    }
+    std::shared_ptr<Ticket>* find(uint64_t id)
+    {
+        const uint64_t slot = id & kSlotMask;
+        if (slot >= slots_.size()) return nullptr;
+        std::shared_ptr<Ticket>& p = slots_[slot];
+        return (p && p->id == id) ? &p : nullptr;
+    }
+    // Removes a ticket found by find(); returns it, so that the caller
+    // decides where the last reference is dropped.
+    std::shared_ptr<Ticket> take(std::shared_ptr<Ticket>* p)
+    {
+        std::shared_ptr<Ticket> t = std::move(*p);
+        free_.push_back((uint32_t)(t->id & kSlotMask));
+        return t;
+    }
+
+private:
+    std::vector<std::shared_ptr<Ticket>> slots_;
+    std::vector<uint32_t> free_;
+};
+
 enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
 enum { kUnclaimed = 0, kClaimedByBatch = 1, kClaimedByCancel = 2 };
 
@@ -358,11 +403,14 @@ public:
             }
             t->pooled = true;
         }
+        t->seq = next_seq_++;
+        if (!tickets_.insert(t, t->seq)) {
+            if (t->pooled) pool_.release(t->pool_block);
+            ++refused_;
+            return fail(XG_EAGAIN, "admission refused: 2^24 tickets outstanding");
+        }
         outstanding_ += t->bytes;
-        t->id = next_id_++;
-        t->seq = t->id;
         t->t_submit = now_ns();
-        tickets_[t->id] = t;
         ++submitted_;
         *ticket = t->id;
         {
@@ -407,19 +455,22 @@ public:
                 out = pool_.alloc(bytes, &block);
                 if (!out) break;
             }
-            made.push_back(std::make_shared<Ticket>());
-            auto& t = made.back();
+            auto t = std::make_shared<Ticket>();
             t->req = reqs[k];
             t->bytes = bytes;
             t->out = out;
             t->pooled = pooled;
             t->pool_block = block;
+            t->seq = next_seq_;
+            if (!tickets_.insert(t, t->seq)) {
+                if (pooled) pool_.release(block);
+                break;
+            }
+            ++next_seq_;
             outstanding_ += t->bytes;
-            t->id = next_id_++;
-            t->seq = t->id;
             t->t_submit = now;
-            tickets_[t->id] = t;
             tickets[k] = t->id;
+            made.push_back(std::move(t));
         }
         submitted_ += k;
         *n_accepted = k;
@@ -441,8 +492,8 @@ public:
     std::shared_ptr<Ticket> find(uint64_t id)
     {
         std::lock_guard<std::mutex> lk(adm_mu_);
-        auto it = tickets_.find(id);
-        return it == tickets_.end() ? nullptr : it->second;
+        std::shared_ptr<Ticket>* p = tickets_.find(id);
+        return p ? *p : nullptr;
     }
 
     bool check_flag(Ticket& t)
@@ -505,9 +556,9 @@ public:
     xg_status release(uint64_t id)
     {
         std::lock_guard<std::mutex> lk(adm_mu_);
-        auto it = tickets_.find(id);
-        if (it == tickets_.end()) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
-        Ticket& t = *it->second;
+        std::shared_ptr<Ticket>* p = tickets_.find(id);
+        if (!p) return fail(XG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)id);
+        Ticket& t = **p;
         if (t.state.load() != kDone && t.state.load() != kFailed && t.state.load() != kCancelled) {
             // the scheduler may not have seen the flag yet
             volatile uint32_t* f = h_flags_ + t.slot;
@@ -516,7 +567,7 @@ public:
         }
         if (t.pooled) pool_.release(t.pool_block);
         outstanding_ -= t.bytes;
-        tickets_.erase(it);
+        tickets_.take(p);
         return XG_OK;
     }
 
@@ -547,8 +598,8 @@ public:
         std::vector<std::shared_ptr<Ticket>> dropped;   // freed after the lock is released
         std::lock_guard<std::mutex> lk(adm_mu_);
         for (auto& t : got) {
-            auto it = tickets_.find(t->id);
-            if (it == tickets_.end()) continue;  // already released by its owner
+            std::shared_ptr<Ticket>* p = tickets_.find(t->id);
+            if (!p) continue;  // already released by its owner
             xg_completion& c = out[n++];
             c.ticket = t->id;
             c.t_submit_ns = t->t_submit;
@@ -561,8 +612,7 @@ public:
             if (release) {
                 if (t->pooled) pool_.release(t->pool_block);
                 outstanding_ -= t->bytes;
-                dropped.push_back(std::move(it->second));
-                tickets_.erase(it);
+                dropped.push_back(tickets_.take(p));
                 c.d_result = nullptr;
             }
         }
@@ -825,9 +875,9 @@ private:
     std::mutex adm_mu_;  // admission: outstanding_, pool_, tickets_, counters (taken before mu_)
     std::mutex mu_;      // incoming_ and cv_
     std::condition_variable cv_;
-    std::unordered_map<uint64_t, std::shared_ptr<Ticket>> tickets_;
+    TicketTable tickets_;
     std::deque<std::shared_ptr<Ticket>> incoming_;
-    uint64_t next_id_ = 1;
+    uint64_t next_seq_ = 1;
     size_t outstanding_ = 0;
     uint64_t submitted_ = 0, refused_ = 0;
     std::atomic<uint64_t> completed_{0}, batches_{0}, items_launched_{0}, queued_{0}, in_flight_{0};
