@@ -40,3 +40,16 @@ def test_plan_batch_invariants(tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
     assert out.stdout.startswith("ok 400"), out.stdout
+
+
+def test_bench_clock_record_rules():
+    """bench.py measures its timed region again when the clock record shows a
+    slowdown reason, or SM clocks well below their maximum with no reason (a
+    leftover clock lock); a power cap alone is kept."""
+    import bench
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench._throttled(ok)
+    assert not bench._throttled(dict(ok, reasons=["sw_power_cap"]))
+    assert bench._throttled(dict(ok, reasons=["hw_thermal_slowdown"]))
+    assert bench._throttled(dict(ok, sm_mhz=1500.0))
+    assert not bench._throttled({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
