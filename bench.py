@@ -776,7 +776,7 @@ def end_to_end(st, stream, torch, L, args, dist=None, ws=1):
 
     step()
     torch.cuda.synchronize()
-    k = max(1, min(args.steps, 3))
+    k = max(1, min(args.steps, 10))
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
