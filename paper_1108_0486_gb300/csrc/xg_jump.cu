@@ -104,11 +104,13 @@ __global__ void __launch_bounds__(64) gf2_apply_kernel(const uint64_t* __restric
 // 5.1 ms with 16 (64 gains no more and needs 168 registers a thread).  Few
 // states take NV = 16, which pads less.
 template <int kPairVecs>
+// rings and out are the same array (sources are read, distinct destinations
+// are written), so neither is declared __restrict__.
 __global__ void __launch_bounds__(128) gf2_apply_pairs_kernel(const uint32_t* __restrict__ C,
-                                                              const uint32_t* __restrict__ rings,
+                                                              const uint32_t* rings,
                                                               const uint32_t* __restrict__ src,
                                                               const uint32_t* __restrict__ dst, uint32_t n,
-                                                              uint32_t* __restrict__ out, int cols)
+                                                              uint32_t* out, int cols)
 {
     __shared__ uint32_t vbits[kPairVecs][kR];
     __shared__ uint32_t tbl[16][kR];
