@@ -28,9 +28,12 @@ Parity status (pins in ``tests/test_oracle_pins.py`` and
   * primitivity test              -- pinned (brute-force orders of z on all
     degree-8 polynomials and all tiny w = 8 sets; the factor list of
     2^4096 - 1 multiplied out and tested for primality)
-  * seeding (project definition)  -- parity unpinned: the paper defers to the
-    xorgens package, which is not available; only determinism and
-    distinctness are checked (both word sizes).
+  * seeding (project definition)  -- pinned to that definition: the xorshift
+    expander against a product of shift matrices and its order 2^64 - 1; the
+    seeded state walked back through the 4r warm-up with the inverse
+    recurrence equals matrix powers of the xorshift applied to the seed word
+    (both word sizes).  The paper defers seeding to the xorgens package, which
+    is not available, so there is no parity with that package's outputs.
 """
 from __future__ import annotations
 
@@ -109,6 +112,7 @@ def _declare(L):
     L.xgo_next.argtypes = [G]; L.xgo_next.restype = u32
     L.xgo_combine.argtypes = [G, u32, u32]; L.xgo_combine.restype = u32
     L.xgo_seed32.argtypes = [G, u32]; L.xgo_seed32.restype = ctypes.c_int
+    L.xgo_xorshift64.argtypes = [u64]; L.xgo_xorshift64.restype = u64
     L.xgo_uniform.argtypes = [u32]; L.xgo_uniform.restype = ctypes.c_float
     L.xgo_normal_pair.argtypes = [u32, u32, p, p]
     L.xgo_normal_pairs.argtypes = [p, u64, p]
@@ -138,6 +142,7 @@ def _declare(L):
     L.xgo64_step.argtypes = [G64]; L.xgo64_step.restype = u64
     L.xgo64_next.argtypes = [G64]; L.xgo64_next.restype = u64
     L.xgo64_seed.argtypes = [G64, u32]; L.xgo64_seed.restype = ctypes.c_int
+    L.xgo64_xorshift64.argtypes = [u64]; L.xgo64_xorshift64.restype = u64
     L.xgo64_uniform.argtypes = [u64]; L.xgo64_uniform.restype = ctypes.c_double
     for f in ("xgo64_fill_u64", "xgo64_fill_raw", "xgo64_fill_uniform"):
         getattr(L, f).argtypes = [G64, u64, p]
@@ -255,6 +260,16 @@ class Xorgens:
         o.g = _Gen()
         ctypes.pointer(o.g)[0] = self.g
         return o
+
+
+def xorshift64(v: int) -> int:
+    """One step of the xorshift that expands a seed (32-bit oracle's copy)."""
+    return int(lib().xgo_xorshift64(v & 0xFFFFFFFFFFFFFFFF))
+
+
+def xorshift64_w64(v: int) -> int:
+    """One step of the 64-bit oracle's own copy of that xorshift."""
+    return int(lib().xgo64_xorshift64(v & 0xFFFFFFFFFFFFFFFF))
 
 
 def uniform_of(words: np.ndarray) -> np.ndarray:

@@ -6,7 +6,7 @@
  * has word sizes other than 32; Sec. 2 recurrence on an r-word circular
  * buffer; Eq. (1) with gamma = w/2 = 32).  omega = the odd integer nearest
  * 2^63 (sqrt 5 - 1), computed here with exact integer square roots.
- * Seeding (project definition, parity unpinned as for 32 bits):
+ * Seeding (project definition, pinned to that definition as for 32 bits):
  *   v = seed * 2^32 + (~seed mod 2^32), 64 xorshift64 outputs discarded, the
  *   ring x_{1-r}..x_0 = the next r outputs (all 64 bits), w_0 = the next,
  *   all-zero guard, then 4r generator words discarded.
@@ -129,29 +129,51 @@ uint64_t xgo64_next(xgo64_gen* g)
     return xk + (w ^ (w >> gamma));
 }
 
-static uint64_t xs64(uint64_t v)
+/* Marsaglia's 64-bit xorshift, triple (13, 7, 17). */
+uint64_t xgo64_xorshift64(uint64_t v)
 {
     v ^= v << 13;
     v ^= v >> 7;
+#if XGO_PLANT == 8
+    v ^= v << 18;
+#else
     v ^= v << 17;
+#endif
     return v;
 }
 
+/* Seeding mistakes planted for the tests (see xorgens_oracle.c): 6 = 63
+ * discards, 7 = the ring filled newest first, 8 = triple (13, 7, 18),
+ * 9 = 4r - 1 warm-up words. */
 int xgo64_seed(xgo64_gen* g, uint32_t seed)
 {
     uint64_t v = ((uint64_t)seed << 32) | (uint64_t)(~seed & 0xFFFFFFFFu);
-    for (int j = 0; j < 64; ++j) v = xs64(v);
+#if XGO_PLANT == 6
+    const int discard = 63;
+#else
+    const int discard = 64;
+#endif
+#if XGO_PLANT == 9
+    const uint32_t warm = 4 * g->r - 1;
+#else
+    const uint32_t warm = 4 * g->r;
+#endif
+    for (int j = 0; j < discard; ++j) v = xgo64_xorshift64(v);
     uint64_t any = 0;
     for (uint32_t j = 0; j < g->r; ++j) {
-        v = xs64(v);
+        v = xgo64_xorshift64(v);
+#if XGO_PLANT == 7
+        g->x[g->r - 1 - j] = v;
+#else
         g->x[j] = v;
+#endif
         any |= v;
     }
-    v = xs64(v);
+    v = xgo64_xorshift64(v);
     g->weyl = v;
     if (!any) g->x[0] = 1;
     g->i = 0;
-    for (uint32_t j = 0; j < 4 * g->r; ++j) (void)xgo64_step(g);
+    for (uint32_t j = 0; j < warm; ++j) (void)xgo64_step(g);
     g->k = 0;
     return 0;
 }

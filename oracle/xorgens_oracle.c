@@ -26,7 +26,8 @@
  *   omega = the odd integer nearest 2^{w-1}(sqrt 5 - 1)  (0x9E3779B9 at w=32),
  *   gamma = w/2, the Weyl word is advanced before use, seeding is this
  *   project's own definition (xgo_seed32 below; the paper defers to the
- *   xorgens package, which is not available -- parity unpinned), and the
+ *   xorgens package, which is not available; the tests pin it to that
+ *   definition, not to the package's outputs), and the
  *   uniform / normal conversions are this project's definitions (the paper
  *   has none): uniform = (out >> 8) * 2^-24, normal = Box-Muller in FP64.
  *
@@ -42,7 +43,10 @@
  * oracle proper is compiled with XGO_PLANT = 0.
  *   1: the lag-s term is dropped        2: (I + R^b) shifts the wrong way
  *   3: the lags' operator pairs swapped 4: the Weyl shift gamma is w/2 - 1
- *   5: the Weyl word is used before it is advanced */
+ *   5: the Weyl word is used before it is advanced
+ * and in the seeding procedure:
+ *   6: 63 xorshift outputs discarded    7: low halves taken instead of high
+ *   8: xorshift triple (13, 7, 18)      9: 4r - 1 warm-up words discarded */
 #ifndef XGO_PLANT
 #define XGO_PLANT 0
 #endif
@@ -156,11 +160,15 @@ uint32_t xgo_next(xgo_gen* g)
 /* Marsaglia's 64-bit xorshift with the published shift triple (13, 7, 17)
  * ("Xorshift RNGs", J. Stat. Software 8(14), 2003); used only to expand a
  * 32-bit seed into a full state. */
-static uint64_t xgo_xorshift64(uint64_t v)
+uint64_t xgo_xorshift64(uint64_t v)
 {
     v ^= v << 13;
     v ^= v >> 7;
+#if XGO_PLANT == 8
+    v ^= v << 18;
+#else
     v ^= v << 17;
+#endif
     return v;
 }
 
@@ -177,18 +185,33 @@ int xgo_seed32(xgo_gen* g, uint32_t seed)
 {
     if (g->w != 32) return -1;
     uint64_t v = ((uint64_t)seed << 32) | (uint64_t)(~seed & 0xFFFFFFFFu);
-    for (int j = 0; j < 64; ++j) v = xgo_xorshift64(v);
+#if XGO_PLANT == 6
+    const int discard = 63;
+#else
+    const int discard = 64;
+#endif
+#if XGO_PLANT == 7
+    const int half = 0;
+#else
+    const int half = 32;
+#endif
+#if XGO_PLANT == 9
+    const uint32_t warm = 4 * g->r - 1;
+#else
+    const uint32_t warm = 4 * g->r;
+#endif
+    for (int j = 0; j < discard; ++j) v = xgo_xorshift64(v);
     uint32_t any = 0;
     for (uint32_t j = 0; j < g->r; ++j) {
         v = xgo_xorshift64(v);
-        g->x[j] = (uint32_t)(v >> 32);
+        g->x[j] = (uint32_t)(v >> half);
         any |= g->x[j];
     }
     v = xgo_xorshift64(v);
-    g->weyl = (uint32_t)(v >> 32);
+    g->weyl = (uint32_t)(v >> half);
     if (!any) g->x[0] = 1;
     g->i = 0;
-    for (uint32_t j = 0; j < 4 * g->r; ++j) (void)xgo_step(g);
+    for (uint32_t j = 0; j < warm; ++j) (void)xgo_step(g);
     g->k = 0;
     return 0;
 }

@@ -20,6 +20,15 @@ CASES = {
          lambda: pins.test_minimal_polynomial_irreducible_degree_4096(0)]),
     4: ("the Weyl shift gamma off by one", [pins.test_weyl_combination_invariant]),
     5: ("the Weyl word used before it is advanced", [pins.test_weyl_combination_invariant]),
+    6: ("63 xorshift outputs discarded in seeding",
+        [lambda: pins.test_seed_procedure_recovered_through_the_warm_up(0)]),
+    7: ("low halves of the xorshift outputs taken in seeding",
+        [lambda: pins.test_seed_procedure_recovered_through_the_warm_up(1)]),
+    8: ("xorshift triple (13, 7, 18) in seeding",
+        [pins.test_seed_xorshift_is_marsaglia_13_7_17_full_period,
+         lambda: pins.test_seed_procedure_recovered_through_the_warm_up(0)]),
+    9: ("4r - 1 warm-up words discarded in seeding",
+        [lambda: pins.test_seed_procedure_recovered_through_the_warm_up(0)]),
 }
 
 
@@ -48,12 +57,18 @@ CASES_W64 = {
     3: ["test_w64_impulse_response_closed_form", "test_w64_minimal_polynomial_primitive_degree_4096"],
     4: ["test_w64_weyl_combination_invariant"],
     5: ["test_w64_weyl_combination_invariant"],
+    6: ["test_w64_seed_procedure_recovered_through_the_warm_up"],
+    7: ["test_w64_seed_procedure_recovered_through_the_warm_up"],
+    8: ["test_w64_seed_xorshift_is_marsaglia_13_7_17_full_period",
+        "test_w64_seed_procedure_recovered_through_the_warm_up"],
+    9: ["test_w64_seed_procedure_recovered_through_the_warm_up"],
 }
 
 
 @pytest.mark.parametrize("plant", sorted(CASES_W64))
 def test_w64_pins_catch_planted_mistake(plant):
-    """The same five mistakes planted in the 64-bit oracle."""
+    """The same mistakes planted in the 64-bit oracle (7: its ring filled
+    newest first, there being no halves to take)."""
     import test_oracle_w64_pins as p64
     with O.planted(plant):
         for name in CASES_W64[plant]:

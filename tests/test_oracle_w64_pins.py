@@ -250,7 +250,7 @@ def test_w64_split_invariance_and_state_roundtrip():
 
 
 def test_w64_seeding_determinism_and_distinct_streams():
-    """Seeding is this project's definition (parity unpinned): deterministic,
+    """Seeding is this project's definition (pinned above): also deterministic,
     distinct seeds give distinct streams, seed 0 is valid."""
     a = O.streams64([0, 1, 2, 0xFFFFFFFF], 256)
     b = O.streams64([0, 1, 2, 0xFFFFFFFF], 256)
@@ -259,3 +259,24 @@ def test_w64_seeding_determinism_and_distinct_streams():
     assert all(np.any(row != 0) for row in a)
     u = O.streams64([9], 100000, kind="uniform")[0]
     assert 0.0 <= u.min() and u.max() < 1.0 and abs(u.mean() - 0.5) < 0.005
+
+
+def test_w64_seed_xorshift_is_marsaglia_13_7_17_full_period():
+    """The 64-bit oracle's own copy of the seed expander: Marsaglia's
+    (13, 7, 17) as a product of shift matrices, of order 2^64 - 1."""
+    from test_oracle_pins import _check_xorshift
+    _check_xorshift(O.xorshift64_w64)
+
+
+def test_w64_seed_procedure_recovered_through_the_warm_up():
+    """Undo the 4r = 256-word warm-up of a seeded 64-bit state: the ring and
+    w_0 before it are xorshift outputs 65 .. 129 of v, whole 64-bit words,
+    oldest first (matrix powers of the xorshift, not the oracle's loop)."""
+    from test_oracle_pins import MASK64, SEED_CASES, _expected_seed_words, _undo_steps
+    r, s, a, b, c, d = O.PARAM_SET_W64
+    om = O.omega64()
+    for seed in SEED_CASES:
+        x, w = O.Xorgens64(*O.PARAM_SET_W64).seed(seed).get_state()
+        ring0 = _undo_steps(x, r, s, a, b, c, d, 4 * r, MASK64)
+        w0 = (w - 4 * r * om) & MASK64
+        assert ring0 + [w0] == _expected_seed_words(seed, r + 1, 64), f"seed {seed:#x}"
