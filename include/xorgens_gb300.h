@@ -53,7 +53,8 @@ typedef enum {
     XG_ETIMEDOUT = 4,  /* a bounded wait gave up */
     XG_ECUDA = 5,      /* a CUDA runtime call failed (message has the CUDA error) */
     XG_ENOTFOUND = 6,  /* unknown ticket */
-    XG_EDEVICE = 7,    /* a kernel reported an internal error through its status word */
+    XG_EDEVICE = 7,    /* device-side state read back by the host is corrupt (xg_get_state),
+                          or a server request's batch failed to launch and never ran */
     XG_ECANCELED = 8   /* the request was cancelled (xg_cancel) before it ran */
 } xg_status;
 
@@ -187,15 +188,17 @@ xg_status xg_generate_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items)
  * cudaMalloc's implicit device synchronisation.  (The paper has no
  * counterpart: this is a property of the library, not of the method.)
  * Calls no cudaMalloc, cudaFree or other allocating routine: the batch
- * description goes to a fixed device array inside the library (about 44 KiB,
- * held by every GPU that loads the library until the process exits) with one
- * cudaMemcpyAsync from a buffer on the calling thread's stack, and the
- * persistent batch kernel of xg_generate_batch runs on it.  Results are
- * identical to xg_generate_batch's.
+ * description is assembled in a fixed host buffer inside the library (about
+ * 86 KiB; calls from several threads take turns on it, and nothing large
+ * goes on the caller's stack) and goes with one cudaMemcpyAsync to a fixed
+ * device array inside the library (about 44 KiB, held by every GPU that
+ * loads the library until the process exits); the persistent batch kernel
+ * of xg_generate_batch runs on it.  Results are identical to
+ * xg_generate_batch's.
  *   - At most 1024 items per call; more is XG_EINVAL.
- *   - The context's device must be current.  The first call on a device looks
- *     up the array's device address (once per device); make that first call
- *     before any stream capture.
+ *   - The context's device must be current.  The array's device address is
+ *     looked up, and the module holding it loaded, by xg_create_streams
+ *     (once per device), so no call of this function loads code or memory.
  *   - The array is shared by every call and keeps the last call's batch; each
  *     call rewrites its header, including the work counter that starts at
  *     zero.  Calls whose kernels overlap on the GPU (different CUDA streams,

@@ -10,6 +10,11 @@
 // persistent batch kernel with its scratch in the file-scope device array
 // below instead.  Every GPU that loads this library holds that array (about
 // 44 KiB) until the process exits.
+//
+// The batch description is assembled in a file-scope host buffer (about
+// 86 KiB with the planner's tables), not on the caller's stack, so threads
+// with small stacks can call this; calls from different threads take turns
+// on that buffer.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -34,10 +39,35 @@ std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 int g_max_grid[kMaxDevices][2] = {};     // persistent grid per device and parameter set
 
+// Host-side planning buffers, one set for the process (guarded by g_stage_mu).
+constexpr uint32_t kSlots = 2 * kNoallocMaxItems;  // stream -> chain, open addressing
+struct Stage {
+    alignas(16) unsigned char desc[kNoallocScratchBytes];  // image of the device scratch
+    uint64_t chain_words[kNoallocMaxItems];
+    uint32_t head_pos[kNoallocMaxItems];
+    uint32_t sorted[kNoallocMaxItems];
+    uint32_t slot_stream[kSlots], slot_last[kSlots], slot_head[kSlots];
+    bool slot_used[kSlots];
+};
+std::mutex g_stage_mu;
+Stage g_stage;
+
+uint64_t item_words(uint32_t type, uint64_t count)
+{
+    return type == XG_NORMAL_F32 ? count + (count & 1u) : count;
+}
+
+}  // namespace
+
+namespace xg {
+
 // Once per device, with that device current: the device address of the
 // array (the host-side symbol is only a stand-in) and the kernel's grid.
-xg_status setup_device(int dev, int sm_count)
+// Called by xg_create_streams, so that the module holding the array and the
+// kernel is loaded there and not by the first xg_generate_batch_noalloc.
+xg_status noalloc_setup(int dev, int sm_count)
 {
+    if (dev < 0 || dev >= kMaxDevices) return XG_OK;  // such a device is refused at call time
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (g_scratch_addr[dev]) return XG_OK;
     void* ptr = nullptr;
@@ -55,12 +85,7 @@ xg_status setup_device(int dev, int sm_count)
     return XG_OK;
 }
 
-uint64_t item_words(uint32_t type, uint64_t count)
-{
-    return type == XG_NORMAL_F32 ? count + (count & 1u) : count;
-}
-
-}  // namespace
+}  // namespace xg
 
 extern "C" xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items, uint32_t n_items)
 {
@@ -71,23 +96,21 @@ extern "C" xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items
     if (n_items > kNoallocMaxItems)
         return fail(XG_EINVAL, "xg_generate_batch_noalloc takes at most %u items per call (got %u)",
                     kNoallocMaxItems, n_items);
-    if (ctx->server) return fail(XG_EINVAL, "the request server owns this context; use xg_submit");
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(XG_EINVAL, "device %d unsupported", ctx->device);
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx->device)
         return fail(XG_EINVAL, "the context's device (%d) must be current (it is %d)", ctx->device, cur);
 
-    // The batch description is built on this thread's stack.
-    alignas(16) unsigned char stage[kNoallocScratchBytes];
-    auto* hdr = reinterpret_cast<xg::BatchHeader*>(stage);
-    auto* heads = reinterpret_cast<uint32_t*>(stage + sizeof(xg::BatchHeader));
-    auto* dev_items = reinterpret_cast<xg::BatchItem*>(stage + kNoallocItemsOffset);
-    uint64_t chain_words[kNoallocMaxItems];
-    uint32_t head_pos[kNoallocMaxItems];
-    // stream -> (last item of its chain, its head position): open addressing
-    constexpr uint32_t kSlots = 2 * kNoallocMaxItems;
-    uint32_t slot_stream[kSlots], slot_last[kSlots], slot_head[kSlots];
-    bool slot_used[kSlots] = {};
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->server) return fail(XG_EINVAL, "the request server owns this context; use xg_submit");
+    if (xg_status st = xg::noalloc_setup(ctx->device, ctx->sm_count)) return st;  // no-op after create
+
+    std::lock_guard<std::mutex> lk_stage(g_stage_mu);
+    Stage& S = g_stage;
+    auto* hdr = reinterpret_cast<xg::BatchHeader*>(S.desc);
+    auto* heads = reinterpret_cast<uint32_t*>(S.desc + sizeof(xg::BatchHeader));
+    auto* dev_items = reinterpret_cast<xg::BatchItem*>(S.desc + kNoallocItemsOffset);
+    std::memset(S.slot_used, 0, sizeof S.slot_used);
     uint32_t n_heads = 0;
     for (uint32_t i = 0; i < n_items; ++i) {
         const xg_item& it = items[i];
@@ -97,38 +120,36 @@ extern "C" xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items
         if (reinterpret_cast<uintptr_t>(it.out) & 3u) return fail(XG_EINVAL, "item %u: output not 4-byte aligned", i);
         dev_items[i] = xg::BatchItem{it.stream, it.type, it.count, it.out, nullptr, xg::kNoItem, 0u};
         uint32_t h = (it.stream * 2654435761u) & (kSlots - 1);
-        while (slot_used[h] && slot_stream[h] != it.stream) h = (h + 1) & (kSlots - 1);
-        if (!slot_used[h]) {
-            slot_used[h] = true;
-            slot_stream[h] = it.stream;
-            slot_last[h] = i;
-            slot_head[h] = n_heads;
+        while (S.slot_used[h] && S.slot_stream[h] != it.stream) h = (h + 1) & (kSlots - 1);
+        if (!S.slot_used[h]) {
+            S.slot_used[h] = true;
+            S.slot_stream[h] = it.stream;
+            S.slot_last[h] = i;
+            S.slot_head[h] = n_heads;
             heads[n_heads] = i;
-            chain_words[n_heads] = item_words(it.type, it.count);
+            S.chain_words[n_heads] = item_words(it.type, it.count);
             ++n_heads;
         } else {
-            dev_items[slot_last[h]].next = i;
-            slot_last[h] = i;
-            chain_words[slot_head[h]] += item_words(it.type, it.count);
+            dev_items[S.slot_last[h]].next = i;
+            S.slot_last[h] = i;
+            S.chain_words[S.slot_head[h]] += item_words(it.type, it.count);
         }
     }
     // longest chain first (ties in submission order)
-    for (uint32_t k = 0; k < n_heads; ++k) head_pos[k] = k;
-    std::sort(head_pos, head_pos + n_heads, [&](uint32_t a, uint32_t b) {
-        return chain_words[a] != chain_words[b] ? chain_words[a] > chain_words[b] : a < b;
+    for (uint32_t k = 0; k < n_heads; ++k) S.head_pos[k] = k;
+    std::sort(S.head_pos, S.head_pos + n_heads, [&](uint32_t a, uint32_t b) {
+        return S.chain_words[a] != S.chain_words[b] ? S.chain_words[a] > S.chain_words[b] : a < b;
     });
-    uint32_t sorted[kNoallocMaxItems];
-    for (uint32_t k = 0; k < n_heads; ++k) sorted[k] = heads[head_pos[k]];
-    std::memcpy(heads, sorted, (size_t)n_heads * 4);
+    for (uint32_t k = 0; k < n_heads; ++k) S.sorted[k] = heads[S.head_pos[k]];
+    std::memcpy(heads, S.sorted, (size_t)n_heads * 4);
     // the work counter starts at zero on every call
     *hdr = xg::BatchHeader{0u, n_heads, n_items, kNoallocMaxItems};
 
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    if (xg_status st = setup_device(ctx->device, ctx->sm_count)) return st;
     void* scratch = g_scratch_addr[ctx->device];
     const size_t used = kNoallocItemsOffset + (size_t)n_items * sizeof(xg::BatchItem);
-    // from pageable stack memory: returns once the source has been read
-    cudaError_t e = cudaMemcpyAsync(scratch, stage, used, cudaMemcpyHostToDevice, ctx->stream);
+    // from pageable host memory: returns once the source has been read, so
+    // the buffer may be reused as soon as this call returns
+    cudaError_t e = cudaMemcpyAsync(scratch, S.desc, used, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return xg::cuda_fail(e, "cudaMemcpyAsync(noalloc batch)");
     xg::BatchArgs a{};
     a.st = ctx->st;

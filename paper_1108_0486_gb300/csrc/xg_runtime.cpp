@@ -279,6 +279,10 @@ xg_status xg_create_streams(xg_ctx** out, uint32_t n_streams, uint32_t param_set
         xg_destroy(c);
         return st;
     }
+    if (xg_status st = xg::noalloc_setup(c->device, c->sm_count)) {
+        xg_destroy(c);
+        return st;
+    }
     *out = c;
     return XG_OK;
 }

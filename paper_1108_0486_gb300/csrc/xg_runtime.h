@@ -15,6 +15,9 @@ class BatchLauncher;
 // Set the calling thread's xg_last_error() message and return st.
 xg_status fail(xg_status st, const char* fmt, ...);
 xg_status cuda_fail(cudaError_t e, const char* what);
+// Device set-up of xg_generate_batch_noalloc (its scratch array's address and
+// the batch kernel's grid), done once per device by xg_create_streams.
+xg_status noalloc_setup(int dev, int sm_count);
 }
 
 struct xg_ctx {
