@@ -13,6 +13,10 @@ the measured HBM peak, per-row figures (normals, fused sum), the SM clocks
 seen during the timed region, and the CPU oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 and no WORLD_SIZE in the environment the script starts N
+ranks of itself (one per GPU) through torch's launcher; under an external
+launcher it runs as the rank it is given.
 """
 from __future__ import annotations
 
@@ -90,6 +94,42 @@ def _issue_ceiling(sm_count, sm_mhz):
     return {"normals_per_s": sm_count * 4 * sm_mhz * 1e6 / per_normal,
             "instructions_per_normal": round(32 * per_normal, 2), "sm_mhz": sm_mhz,
             "source": "profiles/gen_kernel_normal_issue.txt (ncu smsp__inst_executed.sum, 16384 x 4096 case)"}
+
+
+def _free_port() -> int:
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_ranks(n: int, argv) -> int:
+    """Run this script as n ranks on one node, one per GPU (torch's elastic
+    launcher, rendezvous on 127.0.0.1): each rank reads RANK, LOCAL_RANK and
+    WORLD_SIZE from its environment and rank 0 prints the line.  Returns the
+    launcher's exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__),
+           *argv]
+    return subprocess.call(cmd)
+
+
+def rank_check(args):
+    """Launcher check without GPU work (not a bench line): every rank joins a
+    gloo group, reports its stream seeds, and rank 0 prints the ranks seen
+    and the slowest rank's time, each rank having taken 1 + rank ms."""
+    import torch.distributed as dist
+    ws, rank, _ = _dist()
+    dist.init_process_group("gloo")
+    seeds = rank_seeds(rank)
+    gathered = [None] * ws
+    dist.all_gather_object(gathered, (rank, int(seeds[0]), int(seeds[-1]), int(seeds.size)))
+    ms = max_over_ranks(1.0 + rank, dist, "cpu")
+    if rank == 0:
+        print(json.dumps({"rank_check": True, "n_gpus": ws, "requested": args.gpus, "ranks": gathered,
+                          "max_ms": ms}), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
 
 
 def _dist():
@@ -210,6 +250,82 @@ def cpu_baseline(target_s: float = 10.0):
             "sample": f"{passes} pass(es) over {n_streams} of the 16384 streams, 2^16 u32 + 2^16 "
                       f"uniforms each ({passes * n_streams * 2 * N_PER} RNs, {dt:.1f} s wall on "
                       f"{cores} threads)"}
+
+
+def _threaded(jobs, cores):
+    """Run the callables in `jobs` on `cores` threads (ctypes releases the
+    GIL inside the oracle); returns the wall time."""
+    parts = [jobs[i::cores] for i in range(cores)]
+    threads = [threading.Thread(target=lambda p=p: [j() for j in p]) for p in parts if p]
+    t0 = time.perf_counter()
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    return time.perf_counter() - t0
+
+
+def _oracle_draw(g, kind, count, chunk=1 << 22):
+    """count outputs of kind 0 u32 / 1 uniform / 2 normal (FP64) from oracle
+    generator g, in chunks (even, so normal pairs stay aligned)."""
+    fn = (g.u32, g.uniform, g.normal64)[kind]
+    while count > 0:
+        m = min(count, chunk)
+        fn(m)
+        count -= m
+
+
+def oracle_row_baselines(target_s: float = 4.0):
+    """The CPU oracle as it stands on the other rows' workloads, each on a
+    bounded sample: c0 one stream of 2^20 words on one thread; the 2^30
+    normals (FP64 oracle) and the uneven batch threaded over streams / items;
+    a 1% sample of the serving requests, each drawn from its stream's fresh
+    seed, threaded over requests."""
+    import oracle as O
+    O.lib()
+    cores = os.cpu_count() or 1
+    out = {}
+    # c0: single stream, single thread, the whole workload
+    g = O.Xorgens.param_set(0).seed(W.SINGLE_STREAM["seed"])
+    t0 = time.perf_counter()
+    g.u32(W.SINGLE_STREAM["n"])
+    dt = time.perf_counter() - t0
+    out["single_stream_2p20_u32"] = {"value": W.SINGLE_STREAM["n"] / dt, "unit": UNIT, "cores": 1,
+                                     "kind": "oracle", "sample": "the whole workload: one stream, 2^20 u32"}
+    # c2: FP64 normals, 2^16 per stream, threaded over a sample of streams
+    n = W.NORMALS["n"]
+    probe = time.perf_counter()
+    O.streams(W.seeds(1), n, kind="normal")
+    per_stream = time.perf_counter() - probe
+    k = int(min(W.NORMALS["streams"], max(cores, cores * target_s / max(per_stream, 1e-6))))
+    seeds = W.seeds(k)
+    dt = _threaded([lambda s=s: O.streams(seeds[s:s + 1], n, kind="normal") for s in range(k)], cores)
+    out["normal"] = {"value": k * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                     "sample": f"{k} of the 16384 streams x 2^16 FP64 normals ({dt:.1f} s wall)"}
+    # c3: the uneven batch, threaded over items; every m-th item
+    items = W.batched_uneven()
+    total = sum(it.count for it in items)
+    rate = k * n / dt * 1.5  # rough mixed-type rate, only to size the sample
+    m = max(1, int(np.ceil(total / (rate * target_s))))
+    pick = items[::m]
+    words = sum(it.count for it in pick)
+    jobs = [lambda it=it: _oracle_draw(O.Xorgens.param_set(0).seed(it.stream + 1), it.kind, it.count)
+            for it in pick]
+    dt = _threaded(jobs, cores)
+    out["batched"] = {"value": words / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                      "sample": f"1 in {m} of the 4096 items ({len(pick)} items, {words} outputs, "
+                                f"{dt:.1f} s wall)"}
+    # c4: a 1% sample of the 10 s serving requests
+    all_reqs = W.serving_requests(n_streams=65536, rate=20000.0, duration=10.0)
+    reqs = all_reqs[::100]
+    words = sum(r.count for r in reqs)
+    jobs = [lambda r=r: _oracle_draw(O.Xorgens.param_set(0).seed(r.stream + 1), r.kind, r.count)
+            for r in reqs]
+    dt = _threaded(jobs, cores)
+    out["serving"] = {"value": words / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                      "sample": f"1 in 100 of the {len(all_reqs)} requests ({len(reqs)} requests, "
+                                f"{words} outputs, each from its stream's fresh seed; {dt:.1f} s wall)"}
+    return out
 
 
 def run_reference(args):
@@ -374,6 +490,10 @@ def run_ours(args):
                 "clocks": clk, "e2e": e2e, "rows": rows}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
+            if rows:
+                for name, base in oracle_row_baselines().items():
+                    if isinstance(rows.get(name), dict):
+                        rows[name]["cpu_baseline"] = base
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -540,13 +660,17 @@ def batched_row(torch, L, stream, peak, reps=3):
             "hbm_floor_ms": total * 4 / peak / 1e6}
 
 
-def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0, lanes=48, split=0,
+def serving_row(torch, L, stream, seconds=10.0, plain_seconds=2.0, rate=20000.0, lanes=48, split=0,
                 plain=True):
     """Open-loop Poisson arrivals at `rate` req/s on 65536 resident streams,
     sizes log-uniform in [2^10, 2^22], 60/30/10 normal/uniform/u32, memory
-    cap 16 GiB (library pool).  Latency = completion seen by the host minus
-    submission.  Then the plain path: one xg_generate_* launch per request on
-    one CUDA stream, same arrivals, latency from CUDA events."""
+    cap 16 GiB (library pool).  Latency = completion (server clock,
+    CLOCK_MONOTONIC) minus the request's scheduled arrival, so a submitter
+    that falls behind shows up as latency; the time from submission is
+    reported beside it.  Then the plain path: one xg_generate_* kernel launch
+    per request (long calls not cut) on one CUDA stream, the same arrivals
+    over `plain_seconds`, latency from the scheduled arrival to the request's
+    CUDA event."""
     import threading as th
     from paper_1108_0486_gb300 import Streams
     S = 65536
@@ -565,8 +689,8 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0,
         # bulk drain: one call returns (and releases) every finished request
         while len(done_times) < n_total:
             got = L.xg_collect(st.ctx, release=True, buf=cbuf)
-            for _, ts, tl, td, status, _ in got:
-                done_times.append((ts, tl, td))
+            for tk, ts, tl, td, status, _ in got:
+                done_times.append((tk, ts, tl, td))
             if not got:
                 time.sleep(0.0002)
 
@@ -574,6 +698,7 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0,
     sys.setswitchinterval(1e-4)
     rt = th.Thread(target=reaper)
     rt.start()
+    t0_ns = time.monotonic_ns()
     t0 = time.perf_counter()
     for r in reqs:
         gap = r.t_arrival - (time.perf_counter() - t0)
@@ -595,15 +720,25 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0,
     wall = time.perf_counter() - t0
     stats = L.xg_server_stats_get(st.ctx)
     L.xg_server_stop(st.ctx)
-    lat = np.array([(d - s) / 1e6 for s, _, d in done_times])
-    qwait = np.array([(l - s) / 1e6 for s, l, _ in done_times])
+    # completions come back in completion order; ticket numbers grow in
+    # submission order, which is arrival order (one submitting thread)
+    done_times.sort(key=lambda x: x[0])
+    assert len(done_times) == len(reqs)
+    arrival_ns = np.array([t0_ns + r.t_arrival * 1e9 for r in reqs])
+    lat = np.array([(d - a) / 1e6 for (_, _, _, d), a in zip(done_times, arrival_ns)])
+    lat_sub = np.array([(d - s) / 1e6 for _, s, _, d in done_times])
+    qwait = np.array([(l - s) / 1e6 for _, s, l, _ in done_times])
     words = sum(r.count for r in reqs)
-    span = (max(d for _, _, d in done_times) - min(s for s, _, _ in done_times)) / 1e9
+    span = (max(d for _, _, _, d in done_times) - t0_ns) / 1e9
     row = {"workload": f"65536 streams, Poisson {rate:.0f} req/s for {seconds:g} s, sizes log-uniform "
                        "[2^10, 2^22], 60/30/10 normal/uniform/u32 (PCG64 seed 486), cap 16 GiB",
            "requests": len(reqs), "rns": words, "rn_s": words / span, "offered_rn_s": words / seconds,
+           "latency_from": "scheduled arrival",
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-           "max_ms": float(lat.max()), "p50_queue_ms": float(np.percentile(qwait, 50)),
+           "max_ms": float(lat.max()),
+           "p50_from_submit_ms": float(np.percentile(lat_sub, 50)),
+           "p99_from_submit_ms": float(np.percentile(lat_sub, 99)),
+           "p50_queue_ms": float(np.percentile(qwait, 50)),
            "p99_queue_ms": float(np.percentile(qwait, 99)), "refused_retries": refused[0],
            "batches": stats["batches"], "mean_batch": stats["items_launched"] / max(1, stats["batches"]),
            "server_thread_launch_busy": stats["host_launch_ns"] / 1e9 / wall, "wall_s": wall,
@@ -611,31 +746,41 @@ def serving_row(torch, L, stream, seconds=2.0, plain_seconds=0.25, rate=20000.0,
     if not plain:
         st.close()
         return row
-    # plain path: one launch per request, in arrival order, on one CUDA stream
-    preqs = [r for r in reqs if r.t_arrival < plain_seconds]
     buf = torch.empty(1 << 22, dtype=torch.int32, device="cuda")
     fns = [L.xg_generate_u32, L.xg_generate_uniform, L.xg_generate_normal]
-    evs = []
-    e0 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    t0 = time.perf_counter()
-    arrivals = []
-    for r in preqs:
-        while time.perf_counter() - t0 < r.t_arrival:
-            pass
-        arrivals.append(time.perf_counter() - t0)
-        fns[r.kind](st.ctx, r.stream, 1, r.count, buf.data_ptr(), r.count)
-        e = torch.cuda.Event(enable_timing=True)
-        e.record(stream)
-        evs.append(e)
-    torch.cuda.synchronize()
-    plat = np.array([e0.elapsed_time(e) / 1e3 - a for e, a in zip(evs, arrivals)]) * 1e3
-    row["plain_one_launch_per_request"] = {
-        "requests": len(preqs), "window_s": plain_seconds,
-        "p50_ms": float(np.percentile(plat, 50)), "p99_ms": float(np.percentile(plat, 99)),
-        "max_ms": float(plat.max()),
-        "note": "same arrivals; a single CUDA stream serialises the launches, so the queue grows"}
+
+    def plain_arm(window):
+        # one xg_generate_* call per request, in arrival order, on one CUDA
+        # stream; latency from the scheduled arrival to the request's event
+        preqs = [r for r in reqs if r.t_arrival < window]
+        evs = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for r in preqs:
+            while time.perf_counter() - t0 < r.t_arrival:
+                pass
+            fns[r.kind](st.ctx, r.stream, 1, r.count, buf.data_ptr(), r.count)
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            evs.append(e)
+        torch.cuda.synchronize()
+        plat = np.array([e0.elapsed_time(e) / 1e3 - r.t_arrival for e, r in zip(evs, preqs)]) * 1e3
+        return {"requests": len(preqs), "window_s": window, "latency_from": "scheduled arrival",
+                "p50_ms": float(np.percentile(plat, 50)), "p99_ms": float(np.percentile(plat, 99)),
+                "max_ms": float(plat.max()), "drain_s": float(e0.elapsed_time(evs[-1]) / 1e3)}
+
+    st.set_batch_split(1)
+    row["plain_one_launch_per_request"] = dict(
+        plain_arm(plain_seconds), kernel_launches_per_request=1,
+        note="same arrivals; each request is one single-stream kernel launch (one warp), and one CUDA "
+             "stream serialises them, so the queue grows")
+    st.set_batch_split(0)
+    row["plain_cut_by_jump_ahead"] = dict(
+        plain_arm(min(plain_seconds, 0.5)),
+        note="context: the same per-request calls with long calls cut into jump-ahead pieces "
+             "(several launches per long request)")
     st.close()
     return row
 
@@ -855,8 +1000,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the extra rows")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
-                    help="arrival window of the serving row (10 s for the full 200K requests)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="arrival window of the serving row (10 s: about 200K requests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default=None, choices=["u32", "uniform", "normal", "normal_sum", "batch", "w64_uniform", "jump"],
                     help="time one kernel's workload alone (profiling case; not a bench line)")
@@ -867,7 +1012,15 @@ def main():
                          "(the block applies to the 64-bit case)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
+    ap.add_argument("--rank-check", action="store_true",
+                    help="check the N-rank launcher on CPU (gloo, no GPU work; not a bench line)")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU, as a scaling run needs; the ranks re-enter here
+        sys.exit(launch_ranks(args.gpus, sys.argv[1:]))
+    if args.rank_check:
+        rank_check(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.n_per:

@@ -28,6 +28,9 @@ Parity status (pins in ``tests/test_oracle_pins.py`` and
   * primitivity test              -- pinned (brute-force orders of z on all
     degree-8 polynomials and all tiny w = 8 sets; the factor list of
     2^4096 - 1 multiplied out and tested for primality)
+  * outputs after a jump of J words (u32_after_jump, u64_after_jump: z^J
+    mod the minimal polynomial, Sec. 2 linearity) -- pinned against stepping
+    the oracle J words for J up to 2^22 + 3
   * seeding (project definition)  -- pinned to that definition: the xorshift
     expander against a product of shift matrices and its order 2^64 - 1; the
     seeded state walked back through the 4r warm-up with the inverse
@@ -481,6 +484,57 @@ class Xorgens64:
         o.g = _Gen64()
         ctypes.pointer(o.g)[0] = self.g
         return o
+
+
+def _jump_words(raw: np.ndarray, J: int, m: int) -> np.ndarray:
+    """Raw words x_{1+J} .. x_{J+m} from raw = x_1, x_2, ... (at least
+    max(8192, 4096 + m) words of the linear part), without stepping J times.
+
+    Sec. 2: the recurrence is linear over GF(2) on an n = 4096-bit state, so
+    every bit position of the raw words is a sequence annihilated by one
+    polynomial P of degree 4096 (found here by Berlekamp-Massey on 2n bits).
+    With z^J = sum_j c_j z^j (mod P), bit b of x_{k+J} is the XOR of bit b
+    of x_{k+j} over the j with c_j = 1 -- the same j for every bit position,
+    so whole words are XORed."""
+    P = minimal_polynomial_of_bits(raw[:8192] & 1)
+    n = len(P) - 1
+    assert n == 4096 and raw.size >= n + m
+    idx = np.nonzero(zpow(P, int(J)))[0]
+    return np.array([np.bitwise_xor.reduce(raw[i + idx]) for i in range(m)], dtype=raw.dtype)
+
+
+def u32_after_jump(seed: int, J: int, m: int, param_set: int = 0, weyl: bool = True) -> np.ndarray:
+    """The m output words that follow the first J outputs of the stream
+    seeded with `seed` (32-bit words): outputs J+1 .. J+m, computed through
+    z^J mod P (see _jump_words) rather than by stepping.  With the Weyl
+    generator on, output k adds w_k (I + R^16) to x_k, w_k = w_0 + k omega
+    (Sec. 1.5, Eq. (1))."""
+    g = Xorgens.param_set(param_set, weyl=False).seed(seed)
+    w0 = g.weyl
+    raw = g.raw(max(8192, 4096 + m))
+    x = _jump_words(raw, J, m).astype(np.uint64)
+    if not weyl:
+        return x.astype(np.uint32)
+    k = np.arange(J + 1, J + m + 1, dtype=object)
+    w = np.array([(w0 + int(v) * omega(32)) & 0xFFFFFFFF for v in k], dtype=np.uint64)
+    return ((x + (w ^ (w >> np.uint64(16)))) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+
+
+def u64_after_jump(seed: int, J: int, m: int, weyl: bool = True) -> np.ndarray:
+    """As u32_after_jump for the 64-bit generator (gamma = 32)."""
+    g = Xorgens64(*PARAM_SET_W64, weyl=False).seed(seed)
+    w0 = g.weyl
+    raw = g.raw(max(8192, 4096 + m))
+    x = _jump_words(raw, J, m)
+    if not weyl:
+        return x
+    M = (1 << 64) - 1
+    om = omega64()
+    out = []
+    for i in range(m):
+        w = (w0 + (J + 1 + i) * om) & M
+        out.append((int(x[i]) + (w ^ (w >> 32))) & M)
+    return np.array(out, dtype=np.uint64)
 
 
 def uniform64_of(words) -> np.ndarray:

@@ -344,7 +344,7 @@ def test_autotune_picks_a_supported_launch_and_leaves_streams_in_place(kind):
 @pytest.mark.parametrize("ps", [0, 1])
 def test_jump_matches_stepping(ps):
     seeds = W.seeds(6, start=40)
-    for J in (1, 63, 64, 4095, 4096, 65537, 1_000_003):
+    for J in (1, 63, 64, 4095, 4096, 65537, 1_000_003, (1 << 22) + 3):
         with Streams(6, param_set=ps, seeds=seeds) as st:
             st.u32(7)          # not at a round boundary
             st.jump(J)
@@ -352,6 +352,39 @@ def test_jump_matches_stepping(ps):
         for i in (0, 5):
             ref = O.Xorgens.param_set(ps).seed(int(seeds[i])).u32(7 + J + 500)[7 + J:]
             assert np.array_equal(got[i], ref), (ps, J, i)
+
+
+@pytest.mark.parametrize("ps", [0, 1])
+def test_jump_far_against_the_oracle(ps):
+    """Jumps far past any stepping distance against the oracle's own jump,
+    which takes z^J modulo the minimal polynomial of the Sec. 2 recurrence
+    (a different route from the GPU's powers of the transition matrix):
+    Weyl generator on and off, all 32 bits of every word."""
+    seeds = W.seeds(3, start=500)
+    for J in ((1 << 32) + 5, (1 << 40) + 12345, 1 << 63, (1 << 64) - 1):
+        for weyl in (True, False):
+            with Streams(3, param_set=ps, seeds=seeds, weyl=weyl) as st:
+                st.jump(J)
+                got = st.u32(64).cpu().numpy().view(np.uint32)
+            for i in (0, 2):
+                ref = O.u32_after_jump(int(seeds[i]), J, 64, param_set=ps, weyl=weyl)
+                assert np.array_equal(got[i], ref), (ps, J, weyl, i)
+
+
+def test_jump_from_a_pending_position_against_the_oracle():
+    """A jump from a position inside a round (words pending), then a cut
+    call across a 2^21-word piece boundary, all against the oracle."""
+    seeds = W.seeds(2, start=900)
+    J = (1 << 45) + 77
+    with Streams(2, seeds=seeds) as st:
+        st.u32(13)
+        st.jump(J)
+        got = st.u32((1 << 21) + 300).cpu().numpy().view(np.uint32)
+    for i in range(2):
+        ref = O.u32_after_jump(int(seeds[i]), 13 + J, 64)
+        assert np.array_equal(got[i][:64], ref)
+        ref = O.u32_after_jump(int(seeds[i]), 13 + J + (1 << 21) - 32, 332)
+        assert np.array_equal(got[i][(1 << 21) - 32:], ref)
 
 
 def test_jump_composes_for_large_distances():
@@ -395,8 +428,12 @@ def test_substreams_far_apart_equal_jumps(q):
         a.seed_substreams(seed, q)
         for i in range(1, 5):
             b.jump(i << q, first=i, count=1)
-        assert torch.equal(a.normal(333), b.normal(333))
         assert np.array_equal(a.checkpoint()["weyl"], b.checkpoint()["weyl"])
+        assert torch.equal(a.normal(333), b.normal(333))
+        got = a.u32(64).cpu().numpy().view(np.uint32)
+    # and against the oracle's jump: stream i is the sequence from word i 2^q
+    for i in (1, 4):
+        assert np.array_equal(got[i], O.u32_after_jump(seed, (i << q) + 334, 64)), i
 
 
 def test_substreams_weyl_off_and_errors():

@@ -319,6 +319,24 @@ def test_fused_normal_sum(tpg, wpl):
         assert abs(float(s[i]) - float(z64.sum())) <= bound
 
 
+def test_fused_normal_sum_full_size_sampled():
+    """The fused sum on the full normals workload (16384 streams x 2^16, the
+    bench's launch): sampled streams against the FP64 oracle sum within the
+    rounding bound of the FP32 summation order."""
+    S, n = W.NORMALS["streams"], W.NORMALS["n"]
+    seeds = W.seeds(S)
+    with Streams(S, seeds=seeds) as st:
+        st.autotune("normal", n)
+        tpg, _ = st.get_launch("normal")
+        s = st.normal_sum(n).cpu().numpy()
+    m = n // tpg + int(math.log2(tpg)) + 2
+    for i in (0, 1, 777, 8191, 12000, S - 1):
+        z64 = O.Xorgens.param_set(0).seed(int(seeds[i])).normal64(n)
+        bound = float(np.abs(z64).sum()) * (NORMAL_TOL_ULP * 2.0**-23 + m * 2.0**-24 / (1 - m * 2.0**-24))
+        assert abs(float(s[i]) - float(z64.sum())) <= bound, i
+    torch.cuda.empty_cache()
+
+
 # ---- host output -----------------------------------------------------------
 
 def test_host_output_matches_device_output():
@@ -416,21 +434,22 @@ def test_argument_errors():
 
 def test_single_stream_beyond_2p32_words():
     """One call of 2^32 + 5 words on one stream (16 GiB; the counts pass
-    32 bits): the head equals the oracle, the tail equals a stream jumped
-    to the same place, and the position is the whole count."""
+    32 bits): the head equals the oracle, the tail and a piece from the
+    middle equal the oracle's jump to the same place (z^J modulo the minimal
+    polynomial), and the position is the whole count."""
     n = (1 << 32) + 5
     with Streams(1, seeds=[77]) as st:
         out = torch.empty(n, dtype=torch.int32, device="cuda")
         st.u32(n, out=out.view(1, n))
         head = u32np(out[:1024])
         tail = u32np(out[n - 1024:])
+        mid = u32np(out[(1 << 31) + 12345:(1 << 31) + 12345 + 256])
         pos = int(st.checkpoint()["pos"][0])
         del out
     assert pos == n
     assert np.array_equal(head, O.Xorgens.param_set(0).seed(77).u32(1024))
-    with Streams(1, seeds=[77]) as j:
-        j.jump(n - 1024)
-        assert np.array_equal(u32np(j.u32(1024))[0], tail)
+    assert np.array_equal(tail, O.u32_after_jump(77, n - 1024, 1024))
+    assert np.array_equal(mid, O.u32_after_jump(77, (1 << 31) + 12345, 256))
     torch.cuda.empty_cache()
 
 

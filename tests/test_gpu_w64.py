@@ -177,6 +177,19 @@ def test_jump_weyl_off_and_subrange(api):
         assert np.array_equal(got[i], g.raw(100)), i
 
 
+def test_jump_far_against_the_oracle(api):
+    """64-bit jumps far past stepping distance against the oracle's jump by
+    z^J modulo the minimal polynomial, Weyl generator on and off."""
+    seeds = [31, 32]
+    for J in ((1 << 32) + 5, (1 << 40) + 12345, 1 << 63):
+        for weyl in (True, False):
+            st = api.Streams64(2, weyl=weyl, seeds=seeds)
+            st.jump(J)
+            got = _u(st.u64(48))
+            for i, sd in enumerate(seeds):
+                assert np.array_equal(got[i], O.u64_after_jump(sd, J, 48, weyl=weyl)), (J, weyl, i)
+
+
 def test_jump_composes_at_large_distances(api):
     """M^a M^b = M^(a+b) for distances up to 2^63, and the Weyl word
     advances by the distance times omega mod 2^64: jumping a then b gives
@@ -212,7 +225,10 @@ def test_substreams_far_apart_equal_jumps(api):
     a.seed_substreams(seed, 37)
     for i in range(1, 4):
         b.jump(i << 37, first=i, count=1)
-    assert np.array_equal(_u(a.u64(200)), _u(b.u64(200)))
+    got = _u(a.u64(200))
+    assert np.array_equal(got, _u(b.u64(200)))
+    for i in (1, 3):
+        assert np.array_equal(got[i][:40], O.u64_after_jump(seed, i << 37, 40)), i
     from paper_1108_0486_gb300 import _lib as L
     with pytest.raises(L.XGError):
         a.seed_substreams(seed, 63, count=3)

@@ -52,3 +52,25 @@ def test_two_ranks_shard_streams_and_take_the_slowest_time():
         assert an == bn == 16384
         assert a1 < b0  # disjoint, consecutive seed ranges
         assert b0 == a0 + 16384
+
+
+def test_bench_gpus_flag_launches_ranks():
+    """`bench.py --gpus 2` without an outer launcher starts two ranks (here
+    in its launcher-check mode, gloo, no GPU work): rank 0 sees both, their
+    seeds are disjoint, and the time is the slowest rank's."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--rank-check"],
+                       capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["n_gpus"] == 2 and line["requested"] == 2
+    ranks = sorted(line["ranks"])
+    assert [x[0] for x in ranks] == [0, 1]
+    (_, a0, a1, an), (_, b0, b1, bn) = ranks
+    assert an == bn == 16384 and a1 < b0 and b0 == a0 + 16384
+    assert line["max_ms"] == pytest.approx(2.0)

@@ -564,3 +564,27 @@ def test_golden_regression():
         ref = np.array([float(l) for l in f if not l.startswith("#")])
     z = O.Xorgens.param_set(0).seed(7).normal64(256)
     assert np.allclose(z, ref, rtol=1e-15, atol=1e-15)
+
+
+# --------------------------------------------------------------- jump-ahead
+
+@pytest.mark.parametrize("ps", [0, 1])
+def test_outputs_after_jump_equal_stepping(ps):
+    """The oracle's jump (z^J mod the minimal polynomial) against stepping
+    one word at a time, Weyl on and off, across round and ring boundaries."""
+    for J in (0, 1, 127, 128, 4095, 4096, 100003, (1 << 22) + 3):
+        for weyl in (False, True):
+            got = O.u32_after_jump(5 + J % 7, J, 40, param_set=ps, weyl=weyl)
+            g = O.Xorgens.param_set(ps, weyl=weyl).seed(5 + J % 7)
+            ref = g.u32(J + 40)[J:]
+            assert np.array_equal(got, ref), (ps, J, weyl)
+
+
+def test_outputs_after_jump_compose():
+    """Jumping a + b words predicts the same words as stepping b words past
+    the prediction window of a jump of a: checked for a distance 2^40 with
+    b small enough to step (z^(a+b) = z^a z^b)."""
+    a, b = (1 << 40) + 3, 1000
+    far = O.u32_after_jump(9, a + b, 30)
+    near = O.u32_after_jump(9, a, b + 30)
+    assert np.array_equal(far, near[b:])

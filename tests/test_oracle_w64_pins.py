@@ -280,3 +280,12 @@ def test_w64_seed_procedure_recovered_through_the_warm_up():
         ring0 = _undo_steps(x, r, s, a, b, c, d, 4 * r, MASK64)
         w0 = (w - 4 * r * om) & MASK64
         assert ring0 + [w0] == _expected_seed_words(seed, r + 1, 64), f"seed {seed:#x}"
+
+
+def test_w64_outputs_after_jump_equal_stepping():
+    for J in (0, 1, 63, 64, 4097, 100003, (1 << 21) + 5):
+        for weyl in (False, True):
+            got = O.u64_after_jump(11, J, 24, weyl=weyl)
+            g = O.Xorgens64(*O.PARAM_SET_W64, weyl=weyl).seed(11)
+            ref = g.u64(J + 24)[J:] if weyl else g.raw(J + 24)[J:]
+            assert np.array_equal(got, ref), (J, weyl)
