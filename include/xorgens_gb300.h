@@ -191,7 +191,7 @@ xg_status xg_generate_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items)
  * description is assembled in a fixed host buffer inside the library (about
  * 86 KiB; calls from several threads take turns on it, and nothing large
  * goes on the caller's stack) and goes with one cudaMemcpyAsync to a fixed
- * device array inside the library (about 44 KiB, held by every GPU that
+ * device array inside the library (about 48 KiB, held by every GPU that
  * loads the library until the process exits); the persistent batch kernel
  * of xg_generate_batch runs on it.  Results are identical to
  * xg_generate_batch's.
@@ -205,6 +205,36 @@ xg_status xg_generate_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items)
  *     other contexts on the same device, other threads) race on the array:
  *     order them on one stream or synchronise between them. */
 xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items, uint32_t n_items);
+
+/* Launch shape of the persistent batch kernel for calls of one output type
+ * (the threads-per-generator choice of Sec. 2's parallel scheme).  Calls of
+ * that type that are alone on their stream in a batch (and pieces of cut
+ * calls) with a 16-byte aligned output run
+ *   (tpg, wpl) = (32, 2): one stream per warp, 2 words per lane per round,
+ *                         64-bit stores;
+ *                (16, 4): two streams per warp side by side, 4 words per lane,
+ *                         128-bit stores;
+ *                (8, 4):  four streams per warp, 128-bit stores.
+ * The batch groups calls of similar length.  Other calls (several calls on
+ * one stream in a batch, unaligned outputs) always run (32, 2), and so do
+ * normals (their transform needs the registers a wider group would take).
+ * Applies to xg_generate_batch, the request server and cut calls.  The
+ * results do not depend on the shape.  Defaults: (8, 4) for u32 and
+ * uniforms, (32, 2) for normals.  XG_EINVAL for another pair, or for
+ * normals other than (32, 2). */
+xg_status xg_set_batch_shape(xg_ctx* ctx, xg_type type, uint32_t tpg, uint32_t wpl);
+xg_status xg_get_batch_shape(xg_ctx* ctx, xg_type type, uint32_t* tpg, uint32_t* wpl);
+
+/* Autotune the batch kernel's shape per output type on the caller's own
+ * batch: for each type present in items, the calls of that type are run as
+ * one batch with every shape (one warm-up and three timed launches, the
+ * median kept), and the fastest shape is kept for the context.  The stream
+ * states are restored afterwards, so the streams do not advance; the items'
+ * output buffers are written.  Synchronous; allocates a copy of the stream
+ * state.  tpg, wpl, ms: arrays of 3 (indexed by xg_type) or null; a type
+ * absent from the batch keeps its shape and reports ms = 0. */
+xg_status xg_autotune_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items, uint32_t* tpg, uint32_t* wpl,
+                            float* ms);
 
 /* Cutting long calls in batches: a call that is alone on its stream in a
  * batch (xg_generate_batch and the request server) and has at least twice

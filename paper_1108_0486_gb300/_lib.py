@@ -79,6 +79,9 @@ SIGNATURES = {
     "xg_generate_batch": [vp, vp, u32],
     "xg_generate_batch_noalloc": [vp, vp, u32],
     "xg_set_batch_split": [vp, u64],
+    "xg_set_batch_shape": [vp, i32, u32, u32],
+    "xg_get_batch_shape": [vp, i32, P_u32, P_u32],
+    "xg_autotune_batch": [vp, vp, u32, vp, vp, vp],
     "xg_jump": [vp, u32, u32, u64],
     "xg_server_start": [vp, vp],
     "xg_server_stop": [vp],
@@ -245,6 +248,27 @@ def xg_generate_batch_noalloc(ctx, items) -> None:
     array; at most 1024."""
     arr = make_items(items)
     call("xg_generate_batch_noalloc", ctypes.c_void_p(ctx), arr, len(arr))
+
+
+def xg_set_batch_shape(ctx, type_, tpg, wpl) -> None:
+    call("xg_set_batch_shape", ctypes.c_void_p(ctx), int(type_), tpg, wpl)
+
+
+def xg_get_batch_shape(ctx, type_):
+    t, w = ctypes.c_uint32(), ctypes.c_uint32()
+    call("xg_get_batch_shape", ctypes.c_void_p(ctx), int(type_), ctypes.byref(t), ctypes.byref(w))
+    return t.value, w.value
+
+
+def xg_autotune_batch(ctx, items):
+    """Per output type: (tpg, wpl, median ms) of the fastest batch shape on
+    the given batch (ms 0 for a type absent from it)."""
+    arr = make_items(items)
+    tpg = (ctypes.c_uint32 * 3)()
+    wpl = (ctypes.c_uint32 * 3)()
+    ms = (ctypes.c_float * 3)()
+    call("xg_autotune_batch", ctypes.c_void_p(ctx), arr, len(arr), tpg, wpl, ms)
+    return [(tpg[k], wpl[k], ms[k]) for k in range(3)]
 
 
 def xg_set_batch_split(ctx, piece_words) -> None:

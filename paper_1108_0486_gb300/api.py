@@ -152,6 +152,20 @@ class Streams:
         L.xg_generate_batch(self.ctx, [(int(s), TYPES[k] if isinstance(k, str) else int(k), int(c),
                                         0 if o is None else o.data_ptr()) for s, k, c, o in items])
 
+    def set_batch_shape(self, kind, tpg: int, wpl: int):
+        """Batch-kernel shape for single calls of one type: (32,2), (16,4) or (8,4)."""
+        L.xg_set_batch_shape(self.ctx, TYPES[kind] if isinstance(kind, str) else int(kind), tpg, wpl)
+
+    def get_batch_shape(self, kind):
+        return L.xg_get_batch_shape(self.ctx, TYPES[kind] if isinstance(kind, str) else int(kind))
+
+    def autotune_batch(self, items) -> dict:
+        """Pick the batch-kernel shape per type on this batch (streams do not
+        advance; the outputs are written).  Returns {kind: (tpg, wpl, ms)}."""
+        res = L.xg_autotune_batch(self.ctx, [(int(s), TYPES[k] if isinstance(k, str) else int(k), int(c),
+                                              0 if o is None else o.data_ptr()) for s, k, c, o in items])
+        return {name: res[TYPES[name]] for name in TYPES}
+
     def set_batch_split(self, piece_words: int):
         """0: automatic, 1: never cut long calls in batches, else the piece length."""
         L.xg_set_batch_split(self.ctx, piece_words)

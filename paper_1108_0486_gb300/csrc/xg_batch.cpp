@@ -156,10 +156,45 @@ static void plan_order(BatchPlan& plan)
     plan.chain_words.swap(cost);
 }
 
-void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan)
+void plan_tasks(BatchPlan& plan, const uint8_t* shapes)
+{
+    plan.tasks.clear();
+    plan.members.clear();
+    plan.tasks.reserve(plan.heads.size());
+    plan.members.reserve(plan.heads.size() + kMemberSlack);
+    uint32_t pending[3][4];
+    uint32_t npend[3] = {0, 0, 0};
+    auto emit_group = [&](uint32_t kind) {
+        const uint32_t sh = shapes[kind];
+        plan.tasks.push_back(task_word(sh, (uint32_t)plan.members.size()));
+        for (uint32_t g = 0; g < shape_group(sh); ++g) plan.members.push_back(g < npend[kind] ? pending[kind][g] : kNoItem);
+        npend[kind] = 0;
+    };
+    for (const uint32_t u : plan.heads) {
+        const BatchItem& it = plan.units[u];
+        // normals always run as chains (see batch_kernel)
+        const uint32_t sh = shapes && it.kind < kNormal ? shapes[it.kind] : kShapeChain;
+        const bool aligned = (reinterpret_cast<uintptr_t>(it.out) & 15u) == 0;
+        if (sh == kShape16x4 || sh == kShape8x4) {
+            if (it.next == kNoItem && aligned) {
+                pending[it.kind][npend[it.kind]++] = u;
+                if (npend[it.kind] == shape_group(sh)) emit_group(it.kind);
+                continue;
+            }
+        }
+        plan.tasks.push_back(task_word(kShapeChain, (uint32_t)plan.members.size()));
+        plan.members.push_back(u);
+    }
+    for (uint32_t k = 0; k < 3; ++k)
+        if (npend[k]) emit_group(k);
+}
+
+void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan,
+                const uint8_t* shapes)
 {
     plan_units(items, n, piece_len, n_streams, plan);
     plan_order(plan);
+    plan_tasks(plan, shapes);
 }
 
 BatchLauncher::~BatchLauncher()
@@ -195,7 +230,7 @@ xg_status BatchLauncher::build_graph(xg_ctx* c)
     args_.omega = c->weyl_on ? 0x9E3779B9u : 0u;
     void* params[] = {&args_};
     cudaKernelNodeParams kp{};
-    kp.func = const_cast<void*>(batch_kernel_ptr((int)c->param_set));
+    kp.func = const_cast<void*>(batch_kernel_ptr((int)c->param_set, false));
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(kBatchBlock);
     kp.sharedMemBytes = 0;
@@ -221,11 +256,14 @@ xg_status BatchLauncher::reserve(xg_ctx* c, uint32_t capacity)
     if (cudaMalloc(&d_scratch_, bytes_) != cudaSuccess) return XG_ENOMEM;
     if (!done_ && cudaEventCreateWithFlags(&done_, cudaEventDisableTiming) != cudaSuccess) return XG_ECUDA;
     capacity_ = cap;
-    int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel_ptr((int)c->param_set), kBatchBlock, 0) !=
-        cudaSuccess)
-        return XG_ECUDA;
-    max_grid_ = std::max(1, blocks) * c->sm_count;
+    for (int g = 0; g < 2; ++g) {
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel_ptr((int)c->param_set, g == 1),
+                                                          kBatchBlock, 0) != cudaSuccess)
+            return XG_ECUDA;
+        max_grid_g_[g] = std::max(1, blocks) * c->sm_count;
+    }
+    max_grid_ = max_grid_g_[0];
     return build_graph(c);
 }
 
@@ -378,11 +416,13 @@ xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cu
     if (xg_status st = reserve(c, nu)) return st;
     if (xg_status st = prologue(c, s)) return st;
     plan_order(plan_);
+    plan_tasks(plan_, c->batch_shape);
     if (units_per_item) std::memcpy(units_per_item, plan_.units_per_item.data(), (size_t)n * 4);
     char* base = static_cast<char*>(h_staging_);
-    BatchHeader hdr{0u, (uint32_t)plan_.heads.size(), nu, capacity_};
+    BatchHeader hdr{0u, (uint32_t)plan_.tasks.size(), nu, capacity_};
     std::memcpy(base, &hdr, sizeof hdr);
-    std::memcpy(base + sizeof hdr, plan_.heads.data(), plan_.heads.size() * 4);
+    std::memcpy(base + sizeof hdr, plan_.tasks.data(), plan_.tasks.size() * 4);
+    std::memcpy(base + batch_members_offset(capacity_), plan_.members.data(), plan_.members.size() * 4);
     std::memcpy(base + batch_items_offset(capacity_), plan_.units.data(), (size_t)nu * sizeof(BatchItem));
     size_t used = batch_items_offset(capacity_) + (size_t)nu * sizeof(BatchItem);
     if (!plan_.pieces.empty()) {
@@ -393,12 +433,15 @@ xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cu
     if (cudaGraphExecMemcpyNodeSetParams1D(exec_, copy_node_, d_scratch_, h_staging_, used,
                                            cudaMemcpyHostToDevice) != cudaSuccess)
         return XG_ECUDA;
+    // the variant with the group paths only when the plan has group tasks
+    bool groups = false;
+    for (const uint32_t t : plan_.tasks) groups = groups || (t >> 28) != kShapeChain;
     const unsigned grid = (unsigned)std::min<uint64_t>(
-        max_grid_, (plan_.heads.size() + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        max_grid_g_[groups ? 1 : 0], (plan_.tasks.size() + kWarpsPerBlock - 1) / kWarpsPerBlock);
     args_.st = c->st;
     void* params[] = {&args_};
     cudaKernelNodeParams kp{};
-    kp.func = const_cast<void*>(batch_kernel_ptr((int)c->param_set));
+    kp.func = const_cast<void*>(batch_kernel_ptr((int)c->param_set, groups));
     kp.gridDim = dim3(std::max(1u, grid));
     kp.blockDim = dim3(kBatchBlock);
     kp.sharedMemBytes = 0;
@@ -437,6 +480,123 @@ extern "C" xg_status xg_generate_batch(xg_ctx* ctx, const xg_item* items, uint32
     if (st != XG_OK) {
         cudaError_t e = cudaGetLastError();
         return fail(st, "batch launch failed (%s)", cudaGetErrorString(e));
+    }
+    return XG_OK;
+}
+
+namespace {
+
+int shape_of(uint32_t tpg, uint32_t wpl)
+{
+    for (uint32_t sh = 0; sh < (uint32_t)xg::kNumShapes; ++sh)
+        if (xg::shape_tpg(sh) == tpg && xg::shape_wpl(sh) == wpl) return (int)sh;
+    return -1;
+}
+
+}  // namespace
+
+extern "C" xg_status xg_set_batch_shape(xg_ctx* ctx, xg_type type, uint32_t tpg, uint32_t wpl)
+{
+    using namespace xg;
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if ((unsigned)type > XG_NORMAL_F32) return fail(XG_EINVAL, "unknown output type");
+    const int sh = shape_of(tpg, wpl);
+    if (sh < 0) return fail(XG_EINVAL, "batch shape (%u, %u) unsupported: (32,2), (16,4) or (8,4)", tpg, wpl);
+    if (type == XG_NORMAL_F32 && sh != (int)kShapeChain)
+        return fail(XG_EINVAL, "normals run (32,2) in batches");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->batch_shape[type] = (uint8_t)sh;
+    return XG_OK;
+}
+
+extern "C" xg_status xg_get_batch_shape(xg_ctx* ctx, xg_type type, uint32_t* tpg, uint32_t* wpl)
+{
+    using namespace xg;
+    if (!ctx || !tpg || !wpl) return fail(XG_EINVAL, "null argument");
+    if ((unsigned)type > XG_NORMAL_F32) return fail(XG_EINVAL, "unknown output type");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *tpg = shape_tpg(ctx->batch_shape[type]);
+    *wpl = shape_wpl(ctx->batch_shape[type]);
+    return XG_OK;
+}
+
+extern "C" xg_status xg_autotune_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items, uint32_t* tpg,
+                                       uint32_t* wpl, float* ms)
+{
+    using namespace xg;
+    if (!ctx) return fail(XG_EINVAL, "null context");
+    if (n_items > 0 && !items) return fail(XG_EINVAL, "null items");
+    if (ctx->server) return fail(XG_EINVAL, "the request server owns this context; stop it first");
+    std::vector<HostItem> by_kind[3];
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const xg_item& it = items[i];
+        if (it.stream >= ctx->n) return fail(XG_EINVAL, "item %u: stream %u out of range", i, it.stream);
+        if (it.type > XG_NORMAL_F32) return fail(XG_EINVAL, "item %u: unknown type %u", i, it.type);
+        if (it.count > 0 && !it.out) return fail(XG_EINVAL, "item %u: null output", i);
+        if (reinterpret_cast<uintptr_t>(it.out) & 3u) return fail(XG_EINVAL, "item %u: output not 4-byte aligned", i);
+        by_kind[it.type].push_back(HostItem{it.stream, it.type, it.count, it.out, nullptr});
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    BatchLauncher*& L = ctx->batch[0];
+    if (!L) L = new (std::nothrow) BatchLauncher();
+    if (!L) return fail(XG_ENOMEM, "host allocation failed");
+    const size_t state_bytes = (size_t)((char*)(ctx->st.pos + ctx->n) - (char*)ctx->state_mem);
+    void* saved = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&saved, state_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(saved, ctx->state_mem, state_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    xg_status st = e == cudaSuccess ? XG_OK : cuda_fail(e, "batch autotune set-up");
+    float best_ms[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < 3 && st == XG_OK; ++k) {
+        if (by_kind[k].empty()) continue;
+        const std::vector<HostItem>& h = by_kind[k];
+        int best = ctx->batch_shape[k];
+        float best_t = 1e30f;
+        const int n_shapes = k == XG_NORMAL_F32 ? 1 : kNumShapes;   // normals: (32,2) only
+        for (int sh = 0; sh < n_shapes && st == XG_OK; ++sh) {
+            ctx->batch_shape[k] = (uint8_t)sh;
+            float t[3] = {0.f, 0.f, 0.f};
+            for (int r = -1; r < 3 && st == XG_OK; ++r) {
+                if (r >= 0) cudaEventRecord(e0, ctx->stream);
+                st = L->launch(ctx, h.data(), (uint32_t)h.size(), ctx->stream);
+                if (st != XG_OK) {
+                    st = fail(st, "batch autotune launch failed (%s)", cudaGetErrorString(cudaGetLastError()));
+                    break;
+                }
+                if (r >= 0) {
+                    cudaEventRecord(e1, ctx->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        st = cuda_fail(cudaGetLastError(), "batch autotune timing");
+                        break;
+                    }
+                    cudaEventElapsedTime(&t[r], e0, e1);
+                }
+            }
+            if (st != XG_OK) break;
+            std::sort(t, t + 3);
+            if (t[1] < best_t) {
+                best_t = t[1];
+                best = sh;
+            }
+        }
+        ctx->batch_shape[k] = (uint8_t)best;
+        best_ms[k] = best_t;
+    }
+    if (saved) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaMemcpyAsync(ctx->state_mem, saved, state_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(saved);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != XG_OK) return st;
+    for (int k = 0; k < 3; ++k) {
+        if (tpg) tpg[k] = shape_tpg(ctx->batch_shape[k]);
+        if (wpl) wpl[k] = shape_wpl(ctx->batch_shape[k]);
+        if (ms) ms[k] = best_ms[k];
     }
     return XG_OK;
 }

@@ -26,6 +26,8 @@ struct HostItem {
 struct BatchPlan {
     std::vector<BatchItem> units;        // device items (whole calls and pieces)
     std::vector<uint32_t> heads;         // chain heads, costliest chain first
+    std::vector<uint32_t> tasks;         // task words (shape << 28 | first member), costliest first
+    std::vector<uint32_t> members;       // chain heads by task; kNoItem fills a group's unused slots
     std::vector<uint64_t> chain_words;   // estimated cost per chain, same order
     std::vector<BatchPiece> pieces;      // ring/weyl pointers filled at launch
     std::vector<uint32_t> piece_stream;  // stream of each piece
@@ -39,8 +41,14 @@ struct BatchPlan {
 
 // Plan a batch.  piece_len: 0 = cut nothing, else a power of two; calls alone
 // on their stream with at least 2 * piece_len words are cut into pieces of
-// piece_len words (the last one shorter).
-void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan);
+// piece_len words (the last one shorter).  shapes (per output type, null =
+// kShapeChain for all): the task shape for single-call chains of that type
+// whose output is 16-byte aligned; every other chain is a chain task.
+void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan,
+                const uint8_t* shapes = nullptr);
+// Tasks from the ordered heads: consecutive single-call chains of one type
+// (hence of similar cost) fill groups of that type's shape.
+void plan_tasks(BatchPlan& plan, const uint8_t* shapes);
 
 class BatchLauncher {
 public:
@@ -80,7 +88,8 @@ private:
     cudaEvent_t done_ = nullptr;
     bool launched_ = false;
     BatchArgs args_{};
-    int max_grid_ = 0;
+    int max_grid_ = 0;          // resident blocks of the variant without group paths
+    int max_grid_g_[2] = {0, 0};  // per variant (without, with group paths)
     BatchPlan plan_;
     // jump-ahead prologue buffers
     void* h_jstage_ = nullptr;

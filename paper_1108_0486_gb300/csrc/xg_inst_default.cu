@@ -15,6 +15,6 @@ cudaError_t launch_gen_default(int cfg, int out_kind, bool vec, int block, const
     return launch_gen_impl<ParamsDefault>(cfg, out_kind, vec, block, a, s);
 }
 
-const void* batch_kernel_ptr_default() { return batch_kernel_ptr<ParamsDefault>(); }
+const void* batch_kernel_ptr_default(bool groups) { return batch_kernel_ptr<ParamsDefault>(groups); }
 
 }  // namespace xg

@@ -15,6 +15,6 @@ cudaError_t launch_gen_paper(int cfg, int out_kind, bool vec, int block, const G
     return launch_gen_impl<ParamsPaper>(cfg, out_kind, vec, block, a, s);
 }
 
-const void* batch_kernel_ptr_paper() { return batch_kernel_ptr<ParamsPaper>(); }
+const void* batch_kernel_ptr_paper(bool groups) { return batch_kernel_ptr<ParamsPaper>(groups); }
 
 }  // namespace xg

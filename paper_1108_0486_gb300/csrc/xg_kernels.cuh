@@ -365,20 +365,19 @@ __global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
     }
 }
 
-// Persistent batch kernel.  Each warp repeatedly takes the next chain head
-// (atomic counter; heads are sorted longest first by the host), then runs
-// every item of that chain -- the calls on one stream, in order -- with 32
-// lanes per stream and 64-word rounds.  Item types may differ.  A long call
-// may arrive cut into pieces (each its own one-item chain) that different
-// warps run at once.  When an item has a completion counter, the warp fences
-// its stores system-wide and adds 1 to it.
+// Persistent batch kernel.  Each warp repeatedly takes the next task
+// (atomic counter; tasks are ordered costliest first by the host).  A chain
+// task runs every item of one chain -- the calls on one stream, in order --
+// with 32 lanes per stream and 64-word rounds; item types may differ.  A
+// group task runs two or four single-call units of one type side by side,
+// 16 or 8 lanes each with four words per lane (128-bit stores); the host
+// groups units of similar cost.  A long call may arrive cut into pieces
+// (each its own unit) that different warps or groups run at once.  When a
+// unit has a completion counter, its lanes fence their stores system-wide
+// and add 1 to it.
 template <class P>
-__device__ __forceinline__ void run_item(const State& st, const BatchItem& it, const BatchPiece* pieces,
-                                         uint32_t omega, int lane)
+__device__ __forceinline__ UnitSrc unit_src(const BatchItem& it, const BatchPiece* pieces)
 {
-    uint32_t* row = reinterpret_cast<uint32_t*>(it.out);
-    const bool vec = (reinterpret_cast<uintptr_t>(row) & 15u) == 0;
-    constexpr unsigned kFull = 0xFFFFFFFFu;
     UnitSrc src;
     if (it.piece) {
         const BatchPiece& pc = pieces[it.piece - 1];
@@ -387,6 +386,17 @@ __device__ __forceinline__ void run_item(const State& st, const BatchItem& it, c
         src.pos_add = pc.item_words;
         src.write_state = pc.last != 0;
     }
+    return src;
+}
+
+template <class P>
+__device__ __forceinline__ void run_item(const State& st, const BatchItem& it, const BatchPiece* pieces,
+                                         uint32_t omega, int lane)
+{
+    uint32_t* row = reinterpret_cast<uint32_t*>(it.out);
+    const bool vec = (reinterpret_cast<uintptr_t>(row) & 15u) == 0;
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    const UnitSrc src = unit_src<P>(it, pieces);
     switch (it.kind) {
     case kU32:
         if (vec) run_stream<P, 32, 2, kU32, true>(st, it.stream, it.count, row, omega, lane, kFull, src);
@@ -403,24 +413,69 @@ __device__ __forceinline__ void run_item(const State& st, const BatchItem& it, c
     }
 }
 
-template <class P>
+// A group task: lane group g (TPG lanes) runs members[first + g], all of
+// them u32 or all uniforms (normals always run as chains: their transform
+// needs the registers that a wider group would take).
+template <class P, int TPG, int WPL>
+__device__ __forceinline__ void run_group(const State& st, const BatchItem* items, const BatchPiece* pieces,
+                                          const uint32_t* members, uint32_t first, uint32_t omega, int lane)
+{
+    const int gl = lane % TPG;
+    const unsigned mask = group_mask<TPG>();
+    const uint32_t kind = items[members[first]].kind;   // one type per group
+    const uint32_t idx = members[first + lane / TPG];
+    if (idx != kNoItem) {
+        const BatchItem it = items[idx];
+        uint32_t* row = reinterpret_cast<uint32_t*>(it.out);   // 16-byte aligned
+        const UnitSrc src = unit_src<P>(it, pieces);
+        if (kind == kU32) run_stream<P, TPG, WPL, kU32, true>(st, it.stream, it.count, row, omega, gl, mask, src);
+        else run_stream<P, TPG, WPL, kUniform, true>(st, it.stream, it.count, row, omega, gl, mask, src);
+        __syncwarp(mask);
+        if (it.flag) {
+            __threadfence_system();
+            __syncwarp(mask);
+            if (gl == 0) atomicAdd_system(it.flag, 1u);
+        }
+    }
+    __syncwarp();
+}
+
+// GROUPS: whether the kernel carries the group paths.  They raise its
+// register count (fewer resident warps), so a batch without group tasks
+// runs the variant without them.
+template <class P, bool GROUPS>
 __global__ void __launch_bounds__(128) batch_kernel(BatchArgs a)
 {
     const int lane = threadIdx.x & 31;
     constexpr unsigned kFull = 0xFFFFFFFFu;
     BatchHeader* hdr = a.hdr;
-    const uint32_t n_heads = hdr->n_heads;
-    const uint32_t* heads = reinterpret_cast<const uint32_t*>(hdr + 1);
+    const uint32_t n_tasks = hdr->n_tasks;
+    const uint32_t* tasks = reinterpret_cast<const uint32_t*>(hdr + 1);
+    const uint32_t* members = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(hdr) +
+                                                                batch_members_offset(hdr->capacity));
     const BatchItem* items = reinterpret_cast<const BatchItem*>(
         reinterpret_cast<const char*>(hdr) + batch_items_offset(hdr->capacity));
     const BatchPiece* pieces = reinterpret_cast<const BatchPiece*>(
         reinterpret_cast<const char*>(hdr) + batch_pieces_offset(hdr->capacity));
     for (;;) {
-        uint32_t h = 0;
-        if (lane == 0) h = atomicAdd(&hdr->counter, 1u);
-        h = __shfl_sync(kFull, h, 0);
-        if (h >= n_heads) break;
-        uint32_t idx = heads[h];
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&hdr->counter, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= n_tasks) break;
+        const uint32_t task = tasks[t];
+        const uint32_t shape = task >> 28;
+        const uint32_t first = task & kTaskFirstMask;
+        if constexpr (GROUPS) {
+            if (shape == kShape8x4) {
+                run_group<P, 8, 4>(a.st, items, pieces, members, first, a.omega, lane);
+                continue;
+            }
+            if (shape == kShape16x4) {
+                run_group<P, 16, 4>(a.st, items, pieces, members, first, a.omega, lane);
+                continue;
+            }
+        }
+        uint32_t idx = members[first];
         while (idx != kNoItem) {
             const BatchItem it = items[idx];
             run_item<P>(a.st, it, pieces, a.omega, lane);
@@ -480,9 +535,10 @@ cudaError_t launch_gen_cfg(int out_kind, bool vec, int block, const GenArgs& a, 
 }
 
 template <class P>
-const void* batch_kernel_ptr()
+const void* batch_kernel_ptr(bool groups)
 {
-    return reinterpret_cast<const void*>(&batch_kernel<P>);
+    return groups ? reinterpret_cast<const void*>(&batch_kernel<P, true>)
+                  : reinterpret_cast<const void*>(&batch_kernel<P, false>);
 }
 
 template <class P>

@@ -66,24 +66,51 @@ struct BatchPiece {
     uint32_t pad;
 };
 
-// Scratch layout of one batch: header, chain heads (u32, longest chain
-// first), then the items at batch_items_offset(capacity).
+// Tasks of the persistent batch kernel.  A warp takes one task at a time.
+// A task word is (shape << 28) | first, `first` indexing the member list:
+//   kShapeChain: members[first] heads one chain (the calls on one stream, in
+//                order, possibly of different types), 32 lanes per stream,
+//                two words per lane per round (64-bit stores);
+//   kShape16x4:  members[first .. first+2) are single-call chains of one
+//                type, 16 lanes each, four words per lane (128-bit stores);
+//   kShape8x4:   members[first .. first+4), 8 lanes each, four words per lane.
+// A group's unused member slots hold kNoItem.  Every grouped unit's output
+// is 16-byte aligned.
+constexpr uint32_t kShapeChain = 0;
+constexpr uint32_t kShape16x4 = 1;
+constexpr uint32_t kShape8x4 = 2;
+constexpr int kNumShapes = 3;
+XG_HD inline uint32_t shape_tpg(uint32_t shape) { return shape == kShape16x4 ? 16u : shape == kShape8x4 ? 8u : 32u; }
+XG_HD inline uint32_t shape_wpl(uint32_t shape) { return shape == kShapeChain ? 2u : 4u; }
+XG_HD inline uint32_t shape_group(uint32_t shape) { return 32u / shape_tpg(shape); }
+XG_HD inline uint32_t task_word(uint32_t shape, uint32_t first) { return (shape << 28) | first; }
+constexpr uint32_t kTaskFirstMask = 0x0FFFFFFFu;
+// Member slots beyond the unit capacity: the partly filled last group of
+// each type adds at most 3 empty slots.
+constexpr uint32_t kMemberSlack = 16;
+
+// Scratch layout of one batch: header, task words (costliest first), member
+// list, then the units at batch_items_offset(capacity) and the pieces.
 struct BatchHeader {
-    uint32_t counter;   // next head to take (reset to 0 by every launch)
-    uint32_t n_heads;
+    uint32_t counter;   // next task to take (reset to 0 by every launch)
+    uint32_t n_tasks;
     uint32_t n_items;
-    uint32_t capacity;  // items the scratch can hold
+    uint32_t capacity;  // units the scratch can hold
 };
 
-XG_HD inline size_t batch_items_offset(uint32_t capacity)
+XG_HD constexpr size_t batch_members_offset(uint32_t capacity)
 {
-    return (sizeof(BatchHeader) + (size_t)capacity * 4 + 15) / 16 * 16;
+    return sizeof(BatchHeader) + (size_t)capacity * 4;
 }
-XG_HD inline size_t batch_pieces_offset(uint32_t capacity)
+XG_HD constexpr size_t batch_items_offset(uint32_t capacity)
+{
+    return (batch_members_offset(capacity) + ((size_t)capacity + kMemberSlack) * 4 + 15) / 16 * 16;
+}
+XG_HD constexpr size_t batch_pieces_offset(uint32_t capacity)
 {
     return batch_items_offset(capacity) + (size_t)capacity * sizeof(BatchItem);
 }
-XG_HD inline size_t batch_scratch_bytes(uint32_t capacity)
+XG_HD constexpr size_t batch_scratch_bytes(uint32_t capacity)
 {
     return batch_pieces_offset(capacity) + (size_t)capacity * sizeof(BatchPiece);
 }
@@ -117,14 +144,16 @@ cudaError_t launch_export_states(const State& st, uint32_t first, uint32_t n, ui
                                  uint64_t* pos, cudaStream_t s);
 cudaError_t launch_import_states(const State& st, uint32_t first, uint32_t n, const uint32_t* rings,
                                  const uint32_t* weyl, const uint64_t* pos, uint32_t weyl_on, cudaStream_t s);
-const void* batch_kernel_ptr(int param_set);
+// The persistent batch kernel of a parameter set; groups: the variant with
+// the group-task paths.
+const void* batch_kernel_ptr(int param_set, bool groups);
 
 // Per parameter set (defined in xg_inst_default.cu / xg_inst_paper.cu).
 cudaError_t launch_seed_default(const State&, const uint32_t*, uint32_t, uint32_t, cudaStream_t);
 cudaError_t launch_seed_paper(const State&, const uint32_t*, uint32_t, uint32_t, cudaStream_t);
 cudaError_t launch_gen_default(int cfg, int out_kind, bool vec, int block, const GenArgs&, cudaStream_t);
 cudaError_t launch_gen_paper(int cfg, int out_kind, bool vec, int block, const GenArgs&, cudaStream_t);
-const void* batch_kernel_ptr_default();
-const void* batch_kernel_ptr_paper();
+const void* batch_kernel_ptr_default(bool groups);
+const void* batch_kernel_ptr_paper(bool groups);
 
 }  // namespace xg

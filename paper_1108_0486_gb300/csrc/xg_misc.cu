@@ -134,9 +134,9 @@ cudaError_t launch_gen(int param_set, int cfg, int out_kind, bool vec, int block
                           : launch_gen_default(cfg, out_kind, vec, block, a, s);
 }
 
-const void* batch_kernel_ptr(int param_set)
+const void* batch_kernel_ptr(int param_set, bool groups)
 {
-    return param_set == 1 ? batch_kernel_ptr_paper() : batch_kernel_ptr_default();
+    return param_set == 1 ? batch_kernel_ptr_paper(groups) : batch_kernel_ptr_default(groups);
 }
 
 }  // namespace xg

@@ -9,7 +9,7 @@
 // not acceptable.  For them, xg_generate_batch_noalloc runs the same
 // persistent batch kernel with its scratch in the file-scope device array
 // below instead.  Every GPU that loads this library holds that array (about
-// 44 KiB) until the process exits.
+// 48 KiB) until the process exits.
 //
 // The batch description is assembled in a file-scope host buffer (about
 // 86 KiB with the planner's tables), not on the caller's stack, so threads
@@ -26,12 +26,12 @@ namespace {
 
 // At most this many items per call.
 constexpr uint32_t kNoallocMaxItems = 1024;
-constexpr size_t kNoallocItemsOffset =
-    (sizeof(xg::BatchHeader) + (size_t)kNoallocMaxItems * 4 + 15) / 16 * 16;
+constexpr size_t kNoallocItemsOffset = xg::batch_items_offset(kNoallocMaxItems);
 constexpr size_t kNoallocScratchBytes = kNoallocItemsOffset + (size_t)kNoallocMaxItems * sizeof(xg::BatchItem);
 
-// The scratch: header (with the work counter), chain heads, items.  Shared by
-// every call on a device and left holding the last call's batch.
+// The scratch: header (with the work counter), task words, chain heads,
+// items.  Shared by every call on a device and left holding the last call's
+// batch.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -75,8 +75,8 @@ xg_status noalloc_setup(int dev, int sm_count)
     if (e != cudaSuccess || !ptr) return xg::cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
     for (int ps = 0; ps < 2; ++ps) {
         int blocks = 0;
-        const void* fn = ps == 1 ? reinterpret_cast<const void*>(&xg::batch_kernel<xg::ParamsPaper>)
-                                 : reinterpret_cast<const void*>(&xg::batch_kernel<xg::ParamsDefault>);
+        const void* fn = ps == 1 ? reinterpret_cast<const void*>(&xg::batch_kernel<xg::ParamsPaper, false>)
+                                 : reinterpret_cast<const void*>(&xg::batch_kernel<xg::ParamsDefault, false>);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, 128, 0);
         if (e != cudaSuccess) return xg::cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         g_max_grid[dev][ps] = std::max(1, blocks) * sm_count;
@@ -108,7 +108,8 @@ extern "C" xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items
     std::lock_guard<std::mutex> lk_stage(g_stage_mu);
     Stage& S = g_stage;
     auto* hdr = reinterpret_cast<xg::BatchHeader*>(S.desc);
-    auto* heads = reinterpret_cast<uint32_t*>(S.desc + sizeof(xg::BatchHeader));
+    auto* tasks = reinterpret_cast<uint32_t*>(S.desc + sizeof(xg::BatchHeader));
+    auto* heads = reinterpret_cast<uint32_t*>(S.desc + xg::batch_members_offset(kNoallocMaxItems));
     auto* dev_items = reinterpret_cast<xg::BatchItem*>(S.desc + kNoallocItemsOffset);
     std::memset(S.slot_used, 0, sizeof S.slot_used);
     uint32_t n_heads = 0;
@@ -142,6 +143,8 @@ extern "C" xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items
     });
     for (uint32_t k = 0; k < n_heads; ++k) S.sorted[k] = heads[S.head_pos[k]];
     std::memcpy(heads, S.sorted, (size_t)n_heads * 4);
+    // one chain task per head (one stream per warp)
+    for (uint32_t k = 0; k < n_heads; ++k) tasks[k] = xg::task_word(xg::kShapeChain, k);
     // the work counter starts at zero on every call
     *hdr = xg::BatchHeader{0u, n_heads, n_items, kNoallocMaxItems};
 
@@ -158,8 +161,8 @@ extern "C" xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items
     const int ps = ctx->param_set == 1 ? 1 : 0;
     const unsigned grid = (unsigned)std::max<uint64_t>(
         1, std::min<uint64_t>((uint64_t)g_max_grid[ctx->device][ps], (n_heads + 3) / 4));
-    if (ps == 1) xg::batch_kernel<xg::ParamsPaper><<<grid, 128, 0, ctx->stream>>>(a);
-    else xg::batch_kernel<xg::ParamsDefault><<<grid, 128, 0, ctx->stream>>>(a);
+    if (ps == 1) xg::batch_kernel<xg::ParamsPaper, false><<<grid, 128, 0, ctx->stream>>>(a);
+    else xg::batch_kernel<xg::ParamsDefault, false><<<grid, 128, 0, ctx->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return xg::cuda_fail(e, "noalloc batch kernel launch");
     return XG_OK;

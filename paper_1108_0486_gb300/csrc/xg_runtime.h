@@ -44,6 +44,10 @@ struct xg_ctx {
     xg::BatchLauncher* batch[2] = {nullptr, nullptr};
     int batch_next = 0;
     uint64_t split_words = 0;  // batch piece length: 0 automatic, 1 never, else forced
+    // batch kernel task shape per output type (xg::kShape*): single-call
+    // chains of that type are grouped; set by xg_set_batch_shape or
+    // xg_autotune_batch
+    uint8_t batch_shape[3] = {xg::kShape8x4, xg::kShape8x4, xg::kShapeChain};
 
     int pick_cfg(int kind, uint32_t nstreams) const;
     int pick_block(int kind, int cfg) const;

@@ -37,10 +37,47 @@ int main()
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t kind = (uint32_t)(rng() % 3);
             const uint64_t count = (rng() % 5 == 0) ? 0 : 1 + rng() % (uint64_t(1) << (rng() % 15));
+            // most outputs 16-byte aligned, some only 4-byte aligned
+            const uintptr_t off = (rng() % 4 == 0) ? 4u * (1 + rng() % 3) : 0u;
             items[i] = HostItem{(uint32_t)(rng() % n_streams), kind, count,
-                                reinterpret_cast<void*>((uintptr_t)(0x100000000ull * (i + 1))), nullptr};
+                                reinterpret_cast<void*>((uintptr_t)(0x100000000ull * (i + 1)) + off), nullptr};
         }
-        xg::plan_batch(items.data(), n, piece, n_streams, plan);
+        uint8_t shapes[3];
+        for (auto& sh : shapes) sh = (uint8_t)(rng() % xg::kNumShapes);
+        xg::plan_batch(items.data(), n, piece, n_streams, plan, (b % 5 == 0) ? nullptr : shapes);
+        // tasks: every head exactly once among the members; groups hold
+        // single-unit chains of one grouped type with 16-byte aligned output
+        {
+            std::vector<int> head_seen(plan.units.size(), 0);
+            for (uint32_t h : plan.heads) head_seen[h] = 1;
+            if (plan.members.size() > plan.heads.size() + xg::kMemberSlack) return fail_at("member slack", b, 0);
+            size_t listed = 0;
+            for (size_t t = 0; t < plan.tasks.size(); ++t) {
+                const uint32_t sh = plan.tasks[t] >> 28, first = plan.tasks[t] & xg::kTaskFirstMask;
+                if (sh >= (uint32_t)xg::kNumShapes) return fail_at("task shape", b, (long)t);
+                const uint32_t G = xg::shape_group(sh);
+                if (first + G > plan.members.size()) return fail_at("task members range", b, (long)t);
+                if (plan.members[first] == xg::kNoItem) return fail_at("empty task", b, (long)t);
+                const uint32_t kind = plan.units[plan.members[first]].kind;
+                bool filler = false;
+                for (uint32_t g = 0; g < G; ++g) {
+                    const uint32_t u = plan.members[first + g];
+                    if (u == xg::kNoItem) { filler = true; continue; }
+                    if (filler) return fail_at("member after filler", b, (long)t);
+                    if (u >= plan.units.size() || head_seen[u] != 1) return fail_at("member not an unlisted head", b, (long)t);
+                    head_seen[u] = 2;
+                    ++listed;
+                    if (sh != xg::kShapeChain) {
+                        const BatchItem& it = plan.units[u];
+                        if (it.kind != kind || kind > 1) return fail_at("group type", b, (long)t);
+                        if (it.next != xg::kNoItem) return fail_at("grouped chain of several units", b, (long)t);
+                        if (reinterpret_cast<uintptr_t>(it.out) & 15u) return fail_at("grouped unaligned output", b, (long)t);
+                        if (b % 5 == 0 || shapes[kind] != sh) return fail_at("group shape not the type's", b, (long)t);
+                    }
+                }
+            }
+            if (listed != plan.heads.size()) return fail_at("heads listed", b, (long)listed);
+        }
         const uint64_t L = plan.pieces.empty() ? 0 : (uint64_t(1) << plan.split_log2);
         if (!plan.pieces.empty() && L != piece) return fail_at("piece length", b, (long)L);
         std::map<uint32_t, int> per_stream;

@@ -96,6 +96,80 @@ def test_batch_mixed_types_uneven_lengths_and_chains(ps):
         check(k, o[:n], ref)
 
 
+SHAPES = [(32, 2), (16, 4), (8, 4)]
+
+
+@pytest.mark.parametrize("ps", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_batch_shapes_against_the_oracle(ps, shape):
+    """u32 and uniform calls alone on their stream run 1, 2 or 4 streams per
+    warp (normals and chains of several calls stay one per warp), with
+    ragged lengths, unaligned outputs (which must not be grouped) and calls
+    cut into pieces: every output against the oracle."""
+    rng = np.random.default_rng(70 + ps)
+    S = 120
+    seeds = W.seeds(S, start=3000)
+    items = random_items(rng, S, 160, max_len=20000)
+    big = torch.zeros(1 << 22, dtype=torch.int32, device="cuda")
+    outs, off = [], 0
+    for j, (_, k, n) in enumerate(items):
+        off += 1 if j % 7 == 3 else 0          # some outputs 4-byte aligned only
+        o = big[off:off + max(n, 1)]
+        outs.append(o if k == "u32" else o.view(torch.float32))
+        off = (off + max(n, 1) + 3) // 4 * 4 + 4
+    with Streams(S, param_set=ps, seeds=seeds) as st:
+        for k in ("u32", "uniform"):
+            st.set_batch_shape(k, *shape)
+            assert st.get_batch_shape(k) == shape
+        st.set_batch_split(2048)
+        st.batch([(s, k, n, o) for (s, k, n), o in zip(items, outs)])
+        torch.cuda.synchronize()
+        after = st.u32(40).cpu().numpy().view(np.uint32)
+    refs = oracle_per_item(seeds, items, ps)
+    for (s, k, n), o, ref in zip(items, outs, refs):
+        if n:
+            check(k, o[:n], ref)
+    # every stream ends where the oracle does
+    total = {}
+    for s_, k, n in items:
+        total[s_] = total.get(s_, 0) + nwords(k, n)
+    for s_ in (0, 5, S - 1):
+        ref = O.Xorgens.param_set(ps).seed(int(seeds[s_])).u32(total.get(s_, 0) + 40)[-40:]
+        assert np.array_equal(after[s_], ref)
+
+
+def test_batch_shape_argument_errors():
+    from paper_1108_0486_gb300 import XGError, _lib as L
+    with Streams(4, seeds=[1, 2, 3, 4]) as st:
+        with pytest.raises(XGError):
+            st.set_batch_shape("u32", 4, 8)
+        with pytest.raises(XGError):
+            st.set_batch_shape("normal", 8, 4)
+        st.set_batch_shape("normal", 32, 2)
+        assert st.get_batch_shape("normal") == (32, 2)
+
+
+def test_autotune_batch_keeps_streams_and_picks_supported_shapes():
+    rng = np.random.default_rng(8)
+    S = 256
+    seeds = W.seeds(S)
+    items = [(s, KINDS[int(rng.integers(0, 3))], int(rng.integers(1000, 60000))) for s in range(S)]
+    outs = [alloc(k, n) for _, k, n in items]
+    with Streams(S, seeds=seeds) as st:
+        res = st.autotune_batch([(s, k, n, o) for (s, k, n), o in zip(items, outs)])
+        for k in ("u32", "uniform"):
+            assert tuple(res[k][:2]) in SHAPES and res[k][2] > 0
+            assert st.get_batch_shape(k) == tuple(res[k][:2])
+        assert tuple(res["normal"][:2]) == (32, 2)
+        # the streams did not advance: a batch now gives the oracle's first words
+        st.batch([(s, k, n, o) for (s, k, n), o in zip(items, outs)])
+        torch.cuda.synchronize()
+    refs = oracle_per_item(seeds, items)
+    for j in (0, 1, 100, 255):
+        s, k, n = items[j]
+        check(k, outs[j][:n], refs[j])
+
+
 def test_batch_equals_plain_calls_bitwise():
     rng = np.random.default_rng(5)
     seeds = W.seeds(64)
