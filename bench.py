@@ -619,6 +619,10 @@ def batched_row(torch, L, stream, peak, reps=3):
     st = Streams(len(items), seeds=seeds, stream=stream)
     spec = [(it.stream, it.kind, it.count, o.data_ptr()) for it, o in zip(items, outs)]
     arr = L.make_items(spec)  # built once, outside the timed region
+    # the batch kernel's shape per output type, tuned on this batch (the
+    # streams are restored, so they do not advance)
+    tuned = L.xg_autotune_batch(st.ctx, arr)
+    shapes = {name: tuned[k][:2] for k, name in enumerate(W.KIND_NAMES)}
     # two warm-up calls: calls alternate between two launchers (so that one
     # can be planned while the other runs), and each sizes its buffers once
     ms = _time(lambda: L.xg_generate_batch(st.ctx, arr), stream, torch, reps=reps, warm=2)
@@ -644,7 +648,17 @@ def batched_row(torch, L, stream, peak, reps=3):
         ms_k = _time(lambda: L.xg_generate_batch(st.ctx, arr_k), stream, torch, reps=reps, warm=2)
         words_k = sum(it.count + (it.count & 1 if k == 2 else 0) for it in items)
         by_type[name] = {"ms": ms_k, "rn_s": total / (ms_k / 1e3),
-                         "hbm_frac": total * 4 / (ms_k / 1e3) / 1e9 / peak, "words": words_k}
+                         "hbm_frac": total * 4 / (ms_k / 1e3) / 1e9 / peak, "words": words_k,
+                         "shape": shapes[name]}
+        if k < 2:
+            # every shape, for the record (the tuned one is restored after)
+            per_shape = {}
+            for tpg, wpl in ((32, 2), (16, 4), (8, 4)):
+                L.xg_set_batch_shape(st.ctx, k, tpg, wpl)
+                per_shape[f"({tpg},{wpl})"] = _time(lambda: L.xg_generate_batch(st.ctx, arr_k), stream, torch,
+                                                    reps=reps, warm=2)
+            L.xg_set_batch_shape(st.ctx, k, *shapes[name])
+            by_type[name]["ms_by_shape"] = per_shape
     longest = max(range(len(items)), key=lambda i: items[i].count)
     one = L.make_items([spec[longest]])
     ms_long = _time(lambda: L.xg_generate_batch(st.ctx, one), stream, torch, reps=reps, warm=2)
@@ -654,6 +668,7 @@ def batched_row(torch, L, stream, peak, reps=3):
     return {"workload": "4096 items (streams 0..4095, seeds 1..4096), lengths log-uniform [2^10, 2^24] "
                         "(PCG64 seed 1108), types uniform over u32/uniform/normal, one graph-replayed launch",
             "rns_total": total, "ms": ms, "rn_s": total / (ms / 1e3), "host_call_ms": min(host),
+            "shapes": shapes, "autotune_ms": {name: tuned[k][2] for k, name in enumerate(W.KIND_NAMES)},
             "ms_by_forced_piece_len": by_piece, "same_lengths_one_type": by_type,
             "hbm_frac": total * 4 / (ms / 1e3) / 1e9 / peak,
             "longest_item": items[longest].count, "longest_item_alone_ms": ms_long,

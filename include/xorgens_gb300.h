@@ -215,13 +215,17 @@ xg_status xg_generate_batch_noalloc(xg_ctx* ctx, const xg_item* items, uint32_t 
  *                (16, 4): two streams per warp side by side, 4 words per lane,
  *                         128-bit stores;
  *                (8, 4):  four streams per warp, 128-bit stores.
- * The batch groups calls of similar length.  Other calls (several calls on
- * one stream in a batch, unaligned outputs) always run (32, 2), and so do
- * normals (their transform needs the registers a wider group would take).
- * Applies to xg_generate_batch, the request server and cut calls.  The
- * results do not depend on the shape.  Defaults: (8, 4) for u32 and
- * uniforms, (32, 2) for normals.  XG_EINVAL for another pair, or for
- * normals other than (32, 2). */
+ * The batch groups calls of similar length, and only calls of at most 1/8
+ * of a resident warp's share of the batch's words (a group runs each of its
+ * calls at 1/2 or 1/4 of a warp's rate, so a group of long calls would
+ * become the batch's tail).  Other calls (longer ones, several calls on one
+ * stream in a batch, unaligned outputs) run (32, 2), and so do normals
+ * (their transform needs the registers a wider group would take).  Applies
+ * to xg_generate_batch, the request server and cut calls.  The results do
+ * not depend on the shape.  Default: (32, 2) for every type.  The
+ * environment variable XG_BATCH_GROUP_MAX_WORDS=<n> replaces the 1/8 rule
+ * by a fixed limit of n words.  XG_EINVAL for another pair, or for normals
+ * other than (32, 2). */
 xg_status xg_set_batch_shape(xg_ctx* ctx, xg_type type, uint32_t tpg, uint32_t wpl);
 xg_status xg_get_batch_shape(xg_ctx* ctx, xg_type type, uint32_t* tpg, uint32_t* wpl);
 

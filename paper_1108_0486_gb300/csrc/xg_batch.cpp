@@ -2,6 +2,7 @@
 #include "xg_batch.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -156,7 +157,7 @@ static void plan_order(BatchPlan& plan)
     plan.chain_words.swap(cost);
 }
 
-void plan_tasks(BatchPlan& plan, const uint8_t* shapes)
+void plan_tasks(BatchPlan& plan, const uint8_t* shapes, uint64_t group_max_words)
 {
     plan.tasks.clear();
     plan.members.clear();
@@ -176,7 +177,7 @@ void plan_tasks(BatchPlan& plan, const uint8_t* shapes)
         const uint32_t sh = shapes && it.kind < kNormal ? shapes[it.kind] : kShapeChain;
         const bool aligned = (reinterpret_cast<uintptr_t>(it.out) & 15u) == 0;
         if (sh == kShape16x4 || sh == kShape8x4) {
-            if (it.next == kNoItem && aligned) {
+            if (it.next == kNoItem && aligned && words_of(it.kind, it.count) <= group_max_words) {
                 pending[it.kind][npend[it.kind]++] = u;
                 if (npend[it.kind] == shape_group(sh)) emit_group(it.kind);
                 continue;
@@ -190,11 +191,11 @@ void plan_tasks(BatchPlan& plan, const uint8_t* shapes)
 }
 
 void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan,
-                const uint8_t* shapes)
+                const uint8_t* shapes, uint64_t group_max_words)
 {
     plan_units(items, n, piece_len, n_streams, plan);
     plan_order(plan);
-    plan_tasks(plan, shapes);
+    plan_tasks(plan, shapes, group_max_words);
 }
 
 BatchLauncher::~BatchLauncher()
@@ -416,7 +417,17 @@ xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cu
     if (xg_status st = reserve(c, nu)) return st;
     if (xg_status st = prologue(c, s)) return st;
     plan_order(plan_);
-    plan_tasks(plan_, c->batch_shape);
+    // group only units of at most 1/8 of a resident warp's share of the
+    // batch (XG_BATCH_GROUP_MAX_WORDS=<n> sets the limit instead)
+    uint64_t group_max = 0;
+    if (const char* env = std::getenv("XG_BATCH_GROUP_MAX_WORDS")) group_max = std::strtoull(env, nullptr, 10);
+    if (group_max == 0) {
+        uint64_t total = 0;
+        for (const BatchItem& u : plan_.units) total += words_of(u.kind, u.count);
+        const uint64_t warps = (uint64_t)std::max(1, max_grid_g_[1]) * kWarpsPerBlock;
+        group_max = std::max<uint64_t>(64, total / warps / 8);
+    }
+    plan_tasks(plan_, c->batch_shape, group_max);
     if (units_per_item) std::memcpy(units_per_item, plan_.units_per_item.data(), (size_t)n * 4);
     char* base = static_cast<char*>(h_staging_);
     BatchHeader hdr{0u, (uint32_t)plan_.tasks.size(), nu, capacity_};

@@ -45,10 +45,12 @@ struct BatchPlan {
 // kShapeChain for all): the task shape for single-call chains of that type
 // whose output is 16-byte aligned; every other chain is a chain task.
 void plan_batch(const HostItem* items, uint32_t n, uint64_t piece_len, uint32_t n_streams, BatchPlan& plan,
-                const uint8_t* shapes = nullptr);
+                const uint8_t* shapes = nullptr, uint64_t group_max_words = ~uint64_t(0));
 // Tasks from the ordered heads: consecutive single-call chains of one type
-// (hence of similar cost) fill groups of that type's shape.
-void plan_tasks(BatchPlan& plan, const uint8_t* shapes);
+// (hence of similar cost) with at most group_max_words words fill groups of
+// that type's shape; longer units stay chains, so that a group (which runs
+// each of its units at 1/G of a warp's rate) never becomes the batch's tail.
+void plan_tasks(BatchPlan& plan, const uint8_t* shapes, uint64_t group_max_words);
 
 class BatchLauncher {
 public:

@@ -47,7 +47,7 @@ struct xg_ctx {
     // batch kernel task shape per output type (xg::kShape*): single-call
     // chains of that type are grouped; set by xg_set_batch_shape or
     // xg_autotune_batch
-    uint8_t batch_shape[3] = {xg::kShape8x4, xg::kShape8x4, xg::kShapeChain};
+    uint8_t batch_shape[3] = {xg::kShapeChain, xg::kShapeChain, xg::kShapeChain};
 
     int pick_cfg(int kind, uint32_t nstreams) const;
     int pick_block(int kind, int cfg) const;

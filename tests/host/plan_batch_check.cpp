@@ -44,7 +44,8 @@ int main()
         }
         uint8_t shapes[3];
         for (auto& sh : shapes) sh = (uint8_t)(rng() % xg::kNumShapes);
-        xg::plan_batch(items.data(), n, piece, n_streams, plan, (b % 5 == 0) ? nullptr : shapes);
+        const uint64_t gmax = (b % 3 == 0) ? ~uint64_t(0) : (uint64_t(1) << (rng() % 14));
+        xg::plan_batch(items.data(), n, piece, n_streams, plan, (b % 5 == 0) ? nullptr : shapes, gmax);
         // tasks: every head exactly once among the members; groups hold
         // single-unit chains of one grouped type with 16-byte aligned output
         {
@@ -72,6 +73,7 @@ int main()
                         if (it.kind != kind || kind > 1) return fail_at("group type", b, (long)t);
                         if (it.next != xg::kNoItem) return fail_at("grouped chain of several units", b, (long)t);
                         if (reinterpret_cast<uintptr_t>(it.out) & 15u) return fail_at("grouped unaligned output", b, (long)t);
+                        if (words_of(it.kind, it.count) > gmax) return fail_at("grouped long unit", b, (long)t);
                         if (b % 5 == 0 || shapes[kind] != sh) return fail_at("group shape not the type's", b, (long)t);
                     }
                 }

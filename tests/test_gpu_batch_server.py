@@ -101,11 +101,13 @@ SHAPES = [(32, 2), (16, 4), (8, 4)]
 
 @pytest.mark.parametrize("ps", [0, 1])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_batch_shapes_against_the_oracle(ps, shape):
+def test_batch_shapes_against_the_oracle(ps, shape, monkeypatch):
     """u32 and uniform calls alone on their stream run 1, 2 or 4 streams per
     warp (normals and chains of several calls stay one per warp), with
     ragged lengths, unaligned outputs (which must not be grouped) and calls
-    cut into pieces: every output against the oracle."""
+    cut into pieces: every output against the oracle.  The group length
+    limit is lifted (a batch this small would otherwise group nothing)."""
+    monkeypatch.setenv("XG_BATCH_GROUP_MAX_WORDS", str(1 << 40))
     rng = np.random.default_rng(70 + ps)
     S = 120
     seeds = W.seeds(S, start=3000)
