@@ -7,6 +7,7 @@
 #include <new>
 #include <numeric>
 
+#include "xg_gf2_tc.h"
 #include "xg_jump.h"
 #include "xg_runtime.h"
 
@@ -307,8 +308,9 @@ xg_status BatchLauncher::grow_jump(size_t want)
 
 xg_status BatchLauncher::reserve_jump(uint32_t pieces, uint32_t pairs)
 {
-    // the layout of prologue(): rings, weyls, streams, skips, pair lists
-    return grow_jump((size_t)pieces * (512 + 4 + 4 + 8 + 64) + (size_t)pairs * 8 + 4096);
+    // the layout of prologue(): rings, weyls, streams, skips, pair lists,
+    // then the tensor-core operand of one doubling step (at most all pieces)
+    return grow_jump((size_t)pieces * (512 + 4 + 4 + 8 + 64) + (size_t)pairs * 8 + 4096 + gf2_tc_scratch_bytes(pieces));
 }
 
 // Start rings of the pieces.  Piece 0 of a call gets the stream's ring
@@ -339,7 +341,11 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
     const size_t off_streams = (off_weyl + (size_t)P * 4 + 15) / 16 * 16;
     const size_t off_skip = (off_streams + (size_t)P * 4 + 15) / 16 * 16;
     const size_t off_lists = off_skip + (size_t)P * 8;
-    const size_t total = off_lists + 2 * npairs * 4 + 16;
+    uint32_t most = 0;
+    for (int b = 0; b < nsteps; ++b) most = std::max(most, per_step[b]);
+    const size_t tc_bytes = gf2_apply_scratch(c->device, most);  // tensor-core operand, when used
+    const size_t off_tc = (off_lists + 2 * npairs * 4 + 16 + 255) / 256 * 256;
+    const size_t total = off_tc + tc_bytes;
     if (total > jbytes_) {
         if (xg_status st = grow_jump(total + total / 2)) return st;
     }
@@ -390,15 +396,15 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
                             reinterpret_cast<uint32_t*>(db + off_weyl), 1u, c->weyl_on ? 0x9E3779B9u : 0u,
                             s) != cudaSuccess)
         return XG_ECUDA;
+    uint8_t* tc_scratch = tc_bytes ? reinterpret_cast<uint8_t*>(db + off_tc) : nullptr;
     for (int b = 0; b < nsteps; ++b) {
         if (per_step[b] == 0) continue;
-        if (zero_rings(reinterpret_cast<uint32_t*>(db + off_rings), reinterpret_cast<const uint32_t*>(db + dst_off[b]),
-                       per_step[b], s) != cudaSuccess)
-            return XG_ECUDA;
-        if (launch_gf2_apply_pairs(mats[b], reinterpret_cast<uint32_t*>(db + off_rings), per_step[b],
-                                   reinterpret_cast<const uint32_t*>(db + src_off[b]),
-                                   reinterpret_cast<const uint32_t*>(db + dst_off[b]), c->sm_count, s) != cudaSuccess)
-            return XG_ECUDA;
+        xg_status st = XG_OK;
+        if (gf2_apply(c->device, (int)c->param_set, plan_.split_log2 + b, reinterpret_cast<uint32_t*>(db + off_rings),
+                      per_step[b], reinterpret_cast<const uint32_t*>(db + src_off[b]),
+                      reinterpret_cast<const uint32_t*>(db + dst_off[b]), tc_scratch, c->sm_count, s,
+                      &st) != cudaSuccess)
+            return st != XG_OK ? st : XG_ECUDA;
     }
     return XG_OK;
 }
@@ -410,6 +416,10 @@ xg_status BatchLauncher::launch(xg_ctx* c, const HostItem* items, uint32_t n, cu
         if (xg_status st = reserve(c, std::max<uint32_t>(n, 64))) return st;
     }
     if (launched_ && cudaEventSynchronize(done_) != cudaSuccess) return XG_ECUDA;
+    // a tensor-core jump-ahead that gave up waiting (in any earlier prologue)
+    // made its pieces' outputs invalid: report it here, the first point at
+    // which the host has synchronised with it
+    if (launched_ && gf2_tc_take_failure()) return XG_EDEVICE;
     // the jump prologue needs only the pieces: enqueue it before ordering the
     // heads, so that the GPU starts while the host finishes the plan
     plan_units(items, n, choose_piece_len(c, items, n, min_piece), c->n, plan_);

@@ -13,9 +13,12 @@
 // the columns selected by v's bits; squaring is applying C to its own columns.
 // The columns of M itself are one step of the recurrence applied to e_j.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
+#include "xg_gf2_tc.h"
 #include "xg_jump.h"
 #include "xg_kernels.cuh"
 #include "xg_runtime.h"
@@ -263,6 +266,70 @@ const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg
     return T.mat[k];
 }
 
+namespace {
+// FP8 copies of the powers for the tensor-core path: 16 MiB each, built on
+// first use and kept until exit.
+std::mutex g_tc_mu;
+uint8_t* g_tc_mats[64][3][kMaxPow] = {};
+
+const uint8_t* jump_matrix_tc(int device, int family, int k, cudaStream_t s, xg_status* st)
+{
+    const uint64_t* C = jump_matrix(device, family, k, s, st);
+    if (!C) return nullptr;
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    uint8_t*& A = g_tc_mats[device][family][k];
+    if (A) return A;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (size_t)kGf2Bits * kGf2Bits);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *st = fail(XG_ENOMEM, "jump tables: cudaMalloc(16 MiB) failed for the FP8 power %d", k);
+        return nullptr;
+    }
+    e = gf2_tc_expand_matrix(C, static_cast<uint8_t*>(p), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // other CUDA streams may use it next
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        *st = cuda_fail(e, "jump tables: FP8 expansion");
+        return nullptr;
+    }
+    A = static_cast<uint8_t*>(p);
+    return A;
+}
+}  // namespace
+
+bool gf2_use_tc(int device, uint32_t n)
+{
+    // read on every call (a few hundred nanoseconds against a matrix application)
+    const char* off = std::getenv("XG_JUMP_TENSOR_CORES");
+    if (off && std::strcmp(off, "0") == 0) return false;
+    const char* v = std::getenv("XG_GF2_TC_MIN_STATES");
+    const uint32_t min_states = v ? (uint32_t)std::strtoul(v, nullptr, 10) : 1024u;
+    return n >= std::max(1u, min_states) && gf2_tc_available(device);
+}
+
+size_t gf2_apply_scratch(int device, uint32_t n)
+{
+    return gf2_use_tc(device, n) ? gf2_tc_scratch_bytes(n) : 0;
+}
+
+cudaError_t gf2_apply(int device, int family, int k, uint32_t* rings, uint32_t n, const uint32_t* d_src,
+                      const uint32_t* d_dst, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st)
+{
+    *st = XG_OK;
+    if (n == 0) return cudaSuccess;
+    if (scratch && gf2_use_tc(device, n)) {
+        const uint8_t* A = jump_matrix_tc(device, family, k, s, st);
+        if (!A) return cudaErrorMemoryAllocation;
+        return gf2_tc_apply(device, A, rings, d_src, n, rings, d_dst, scratch, s);
+    }
+    const uint64_t* C = jump_matrix(device, family, k, s, st);
+    if (!C) return cudaErrorMemoryAllocation;
+    cudaError_t e = zero_rings(rings, d_dst, n, s);
+    if (e == cudaSuccess) e = launch_gf2_apply_pairs(C, rings, n, d_src, d_dst, sm_count, s);
+    return e;
+}
+
 template <int NV>
 static cudaError_t launch_pairs(const uint64_t* C, uint32_t* rings, uint32_t n, const uint32_t* d_src,
                                 const uint32_t* d_dst, int sm_count, cudaStream_t s)
@@ -321,8 +388,11 @@ extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uin
     // swap roles after every set bit of words.
     uint32_t* rings = nullptr;
     uint32_t* ids = nullptr;   // [0, 2n): stream ids for the gather, then 0..2n-1
+    uint8_t* scratch = nullptr;  // tensor-core operand (when used)
+    const size_t sbytes = gf2_apply_scratch(ctx->device, nstreams);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)2 * nstreams * kR * 4, s);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)3 * nstreams * 4, s);
+    if (e == cudaSuccess && sbytes) e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sbytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "xg_jump scratch");
     std::vector<uint32_t> h((size_t)3 * nstreams);
     for (uint32_t i = 0; i < nstreams; ++i) h[i] = first + i;
@@ -334,11 +404,9 @@ extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uin
     bool in_lo = true;
     for (int k = 0; k <= top && e == cudaSuccess; ++k) {
         if (!((words >> k) & 1)) continue;
-        const uint64_t* C = jump_matrix(ctx->device, (int)ctx->param_set, k, s, &st);
         const uint32_t* src = in_lo ? lo_idx : hi_idx;
         const uint32_t* dst = in_lo ? hi_idx : lo_idx;
-        e = zero_rings(rings, dst, nstreams, s);
-        if (e == cudaSuccess) e = launch_gf2_apply_pairs(C, rings, nstreams, src, dst, ctx->sm_count, s);
+        e = gf2_apply(ctx->device, (int)ctx->param_set, k, rings, nstreams, src, dst, scratch, ctx->sm_count, s, &st);
         in_lo = !in_lo;
     }
     if (e == cudaSuccess) {
@@ -350,7 +418,11 @@ extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uin
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
     cudaFreeAsync(rings, s);
     cudaFreeAsync(ids, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (st != XG_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "xg_jump");
+    if (sbytes && gf2_tc_take_failure())
+        return fail(XG_EDEVICE, "xg_jump: a tensor-core kernel gave up waiting; the streams are not valid");
     return XG_OK;
 }
 
@@ -391,22 +463,24 @@ extern "C" xg_status xg_seed_substreams(xg_ctx* ctx, uint32_t first, uint32_t co
     }
     uint32_t* rings = nullptr;
     uint32_t* lists = nullptr;   // the host lists, then the gathered Weyl word
+    uint8_t* scratch = nullptr;  // tensor-core operand (when used)
+    const uint32_t most = steps ? *std::max_element(cnt.begin(), cnt.end()) : 0u;
+    const size_t sbytes = gf2_apply_scratch(ctx->device, most);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)count * kR * 4, s);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&lists), (h.size() + 1) * 4, s);
+    if (e == cudaSuccess && sbytes) e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sbytes, s);
     if (e != cudaSuccess) {
         if (rings) cudaFreeAsync(rings, s);
+        if (lists) cudaFreeAsync(lists, s);
         return cuda_fail(e, "xg_seed_substreams scratch");
     }
     uint32_t* d_w0 = lists + h.size();
     e = cudaMemcpyAsync(lists, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = launch_gather_rings(ctx->st, lists, 1, rings, nullptr, d_w0, 1, 0u, s);
-    for (int b = 0; b < steps && e == cudaSuccess; ++b) {
-        const uint64_t* C = jump_matrix(ctx->device, (int)ctx->param_set, q + b, s, &st);
-        e = zero_rings(rings, lists + dst_off[b], cnt[b], s);
-        if (e == cudaSuccess)
-            e = launch_gf2_apply_pairs(C, rings, cnt[b], lists + src_off[b], lists + dst_off[b], ctx->sm_count, s);
-    }
+    for (int b = 0; b < steps && e == cudaSuccess; ++b)
+        e = gf2_apply(ctx->device, (int)ctx->param_set, q + b, rings, cnt[b], lists + src_off[b], lists + dst_off[b],
+                      scratch, ctx->sm_count, s, &st);
     if (e == cudaSuccess) {
         substream_scatter_kernel<<<count, 128, 0, s>>>(ctx->st, first, count, rings, d_w0, q,
                                                        ctx->weyl_on ? 0x9E3779B9u : 0u);
@@ -415,6 +489,10 @@ extern "C" xg_status xg_seed_substreams(xg_ctx* ctx, uint32_t first, uint32_t co
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
     cudaFreeAsync(rings, s);
     cudaFreeAsync(lists, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (st != XG_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "xg_seed_substreams");
+    if (sbytes && gf2_tc_take_failure())
+        return fail(XG_EDEVICE, "xg_seed_substreams: a tensor-core kernel gave up waiting; the streams are not valid");
     return XG_OK;
 }

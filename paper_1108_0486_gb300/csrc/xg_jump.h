@@ -23,6 +23,21 @@ const uint64_t* jump_matrix(int device, int param_set, int k, cudaStream_t s, xg
 cudaError_t launch_gf2_apply_pairs(const uint64_t* C, uint32_t* rings, uint32_t n, const uint32_t* d_src,
                                    const uint32_t* d_dst, int sm_count, cudaStream_t s);
 
+// Whether an application to n states runs on the tensor cores (sm_103 and
+// n >= XG_GF2_TC_MIN_STATES, default 1024; XG_JUMP_TENSOR_CORES=0 turns the
+// tensor-core path off), and the device scratch it then needs (0 otherwise).
+bool gf2_use_tc(int device, uint32_t n);
+size_t gf2_apply_scratch(int device, uint32_t n);
+
+// rings[d_dst[i]] = C_k rings[d_src[i]] for n pairs, C_k the power 2^k of
+// the matrix family (destinations distinct and not among the sources).  On
+// the tensor cores when gf2_use_tc(device, n) and scratch (gf2_apply_scratch
+// bytes) is given, else with the table kernel.  Asynchronous on s, except
+// that a power's first use builds it.  After synchronising, a caller that
+// may have used the tensor cores checks gf2_tc_take_failure().
+cudaError_t gf2_apply(int device, int family, int k, uint32_t* rings, uint32_t n, const uint32_t* d_src,
+                      const uint32_t* d_dst, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st);
+
 // rings[d_idx[i]] = 0 for n listed 128-word rings.
 cudaError_t zero_rings(uint32_t* rings, const uint32_t* d_idx, uint32_t n, cudaStream_t s);
 

@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "xg_gf2_tc.h"
 #include "xg_jump.h"
 #include "xg_runtime.h"
 #include "xg_w64.h"
@@ -132,7 +133,10 @@ xg_status generate_cut(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstream
     const size_t off_pos = off_weyl + (size_t)P * 8;
     const size_t off_pend = off_pos + (size_t)P * 8;
     const size_t off_lists = align_up(off_pend + (size_t)P * 4, 16);
-    const size_t total = off_lists + h.size() * 4 + 4;
+    const uint32_t most = steps ? *std::max_element(cnt.begin(), cnt.end()) : 0u;
+    const size_t tc_bytes = xg::gf2_apply_scratch(c->device, most);  // tensor-core operand, when used
+    const size_t off_tc = align_up(off_lists + h.size() * 4 + 4, 256);
+    const size_t total = off_tc + tc_bytes;
     char* scratch = nullptr;
     XG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, s), "cut scratch");
     uint64_t* rings = reinterpret_cast<uint64_t*>(scratch);
@@ -145,12 +149,10 @@ xg_status generate_cut(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstream
     // piece 0 of each stream: the stream's own ring (gathered one stream at a time)
     for (uint32_t i = 0; i < nstreams && e == cudaSuccess; ++i)
         e = xg64::launch_gather_rings(c->st, first + i, 1, rings + (size_t)i * K * xg64::kR, s);
-    for (int b = 0; b < steps && e == cudaSuccess; ++b) {
-        const uint64_t* C = xg::jump_matrix(c->device, xg::kJumpSetW64, q + b, s, &st);
-        e = xg::zero_rings(rings32, lists + dst_off[b], cnt[b], s);
-        if (e == cudaSuccess)
-            e = xg::launch_gf2_apply_pairs(C, rings32, cnt[b], lists + src_off[b], lists + dst_off[b], c->sm_count, s);
-    }
+    uint8_t* tc_scratch = tc_bytes ? reinterpret_cast<uint8_t*>(scratch + off_tc) : nullptr;
+    for (int b = 0; b < steps && e == cudaSuccess; ++b)
+        e = xg::gf2_apply(c->device, xg::kJumpSetW64, q + b, rings32, cnt[b], lists + src_off[b], lists + dst_off[b],
+                          tc_scratch, c->sm_count, s, &st);
     const uint64_t omega = c->weyl_on ? xg64::kOmega : 0;
     if (e == cudaSuccess) e = xg64::launch_init_pieces(c->st, first, nstreams, K, L, rings, pieces, omega, s);
     xg_status gst = XG_OK;
@@ -400,10 +402,14 @@ xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t
     // four-column table kernel works on 4096-bit states as 128 32-bit words)
     uint64_t* rings = nullptr;
     uint32_t* ids = nullptr;   // 0 .. 2n-1
+    uint8_t* tc_scratch = nullptr;  // tensor-core operand, when used
+    const size_t tc_bytes = xg::gf2_apply_scratch(c->device, nstreams);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)2 * nstreams * xg64::kR * 8, s);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)2 * nstreams * 4, s);
+    if (e == cudaSuccess && tc_bytes) e = cudaMallocAsync(reinterpret_cast<void**>(&tc_scratch), tc_bytes, s);
     if (e != cudaSuccess) {
         if (rings) cudaFreeAsync(rings, s);
+        if (ids) cudaFreeAsync(ids, s);
         return cuda_fail(e, "xg_w64_jump scratch");
     }
     std::vector<uint32_t> h((size_t)2 * nstreams);
@@ -416,11 +422,9 @@ xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t
     bool in_lo = true;
     for (int k = 0; k <= top && e == cudaSuccess; ++k) {
         if (!((words >> k) & 1)) continue;
-        const uint64_t* C = xg::jump_matrix(c->device, xg::kJumpSetW64, k, s, &st);
         const uint32_t* src = in_lo ? lo_idx : hi_idx;
         const uint32_t* dst = in_lo ? hi_idx : lo_idx;
-        e = xg::zero_rings(rings32, dst, nstreams, s);
-        if (e == cudaSuccess) e = xg::launch_gf2_apply_pairs(C, rings32, nstreams, src, dst, c->sm_count, s);
+        e = xg::gf2_apply(c->device, xg::kJumpSetW64, k, rings32, nstreams, src, dst, tc_scratch, c->sm_count, s, &st);
         in_lo = !in_lo;
     }
     if (e == cudaSuccess) {
@@ -430,7 +434,11 @@ xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
     cudaFreeAsync(rings, s);
     cudaFreeAsync(ids, s);
+    if (tc_scratch) cudaFreeAsync(tc_scratch, s);
+    if (st != XG_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "xg_w64_jump");
+    if (tc_bytes && xg::gf2_tc_take_failure())
+        return fail(XG_EDEVICE, "xg_w64_jump: a tensor-core kernel gave up waiting; the streams are not valid");
     return XG_OK;
 }
 
@@ -466,11 +474,16 @@ xg_status xg_w64_seed_substreams(xg_w64_ctx* c, uint32_t first, uint32_t count, 
     }
     uint64_t* rings = nullptr;
     uint32_t* lists = nullptr;   // the pair lists, then (8-byte aligned) the base Weyl word
+    uint8_t* tc_scratch = nullptr;  // tensor-core operand, when used
+    const uint32_t most = steps ? *std::max_element(cnt.begin(), cnt.end()) : 0u;
+    const size_t tc_bytes = xg::gf2_apply_scratch(c->device, most);
     const size_t w0_off = (h.size() * 4 + 7) / 8 * 8;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)count * xg64::kR * 8, s);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&lists), w0_off + 8, s);
+    if (e == cudaSuccess && tc_bytes) e = cudaMallocAsync(reinterpret_cast<void**>(&tc_scratch), tc_bytes, s);
     if (e != cudaSuccess) {
         if (rings) cudaFreeAsync(rings, s);
+        if (lists) cudaFreeAsync(lists, s);
         return cuda_fail(e, "xg_w64_seed_substreams scratch");
     }
     uint64_t* d_w0 = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(lists) + w0_off);
@@ -478,18 +491,19 @@ xg_status xg_w64_seed_substreams(xg_w64_ctx* c, uint32_t first, uint32_t count, 
     e = cudaMemcpyAsync(lists, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_w0, c->st.weyl + first, 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = xg64::launch_gather_rings(c->st, first, 1, rings, s);
-    for (int b = 0; b < steps && e == cudaSuccess; ++b) {
-        const uint64_t* C = xg::jump_matrix(c->device, xg::kJumpSetW64, q + b, s, &st);
-        e = xg::zero_rings(rings32, lists + dst_off[b], cnt[b], s);
-        if (e == cudaSuccess)
-            e = xg::launch_gf2_apply_pairs(C, rings32, cnt[b], lists + src_off[b], lists + dst_off[b], c->sm_count, s);
-    }
+    for (int b = 0; b < steps && e == cudaSuccess; ++b)
+        e = xg::gf2_apply(c->device, xg::kJumpSetW64, q + b, rings32, cnt[b], lists + src_off[b], lists + dst_off[b],
+                          tc_scratch, c->sm_count, s, &st);
     if (e == cudaSuccess)
         e = xg64::launch_substream_scatter(c->st, first, count, rings, d_w0, q, c->weyl_on ? xg64::kOmega : 0, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
     cudaFreeAsync(rings, s);
     cudaFreeAsync(lists, s);
+    if (tc_scratch) cudaFreeAsync(tc_scratch, s);
+    if (st != XG_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "xg_w64_seed_substreams");
+    if (tc_bytes && xg::gf2_tc_take_failure())
+        return fail(XG_EDEVICE, "xg_w64_seed_substreams: a tensor-core kernel gave up waiting; the streams are not valid");
     return XG_OK;
 }
 

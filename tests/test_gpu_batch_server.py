@@ -463,6 +463,70 @@ def test_jump_from_a_pending_position_against_the_oracle():
         assert np.array_equal(got[i][(1 << 21) - 32:], ref)
 
 
+# ---- the tensor-core path of the jump-ahead (tcgen05, FP8 0/1 operands) ----
+
+def _jump_states(S, J, ps=0, monkeypatch=None, tc=True, seeds=None):
+    if monkeypatch is not None:
+        monkeypatch.setenv("XG_JUMP_TENSOR_CORES", "1" if tc else "0")
+    seeds = W.seeds(S, start=7000) if seeds is None else seeds
+    with Streams(S, param_set=ps, seeds=seeds) as st:
+        st.u32(5)                      # words pending: the jump starts inside a round
+        st.jump(J)
+        ck = st.checkpoint()
+        words = st.u32(48).cpu().numpy().view(np.uint32)
+    return ck, words, seeds
+
+
+@pytest.mark.parametrize("ps", [0, 1])
+def test_jump_tensor_cores_against_the_table_kernel_and_the_oracle(ps, monkeypatch):
+    """2304 streams (nine tiles of 256 states, the last one partly padding
+    after 2048 + 256): the tensor-core application equals the table kernel
+    bit for bit on every stream, and sampled streams equal the oracle's
+    jump (z^J modulo the minimal polynomial)."""
+    J = (1 << 40) + 12345
+    S = 2304 - 100
+    a, wa, seeds = _jump_states(S, J, ps, monkeypatch, tc=True)
+    b, wb, _ = _jump_states(S, J, ps, monkeypatch, tc=False)
+    assert np.array_equal(a["rings"], b["rings"]) and np.array_equal(a["weyl"], b["weyl"])
+    assert np.array_equal(wa, wb)
+    for i in (0, 255, 256, 1777, S - 1):
+        assert np.array_equal(wa[i], O.u32_after_jump(int(seeds[i]), 5 + J, 48, param_set=ps)), i
+
+
+def test_jump_tensor_cores_small_and_partial_tiles(monkeypatch):
+    """With the threshold lowered, 1, 37 and 300 states run on the tensor
+    cores (one partly filled tile, and a second one nearly empty)."""
+    monkeypatch.setenv("XG_GF2_TC_MIN_STATES", "1")
+    for S in (1, 37, 300):
+        a, wa, seeds = _jump_states(S, (1 << 63) + 99, 0, monkeypatch, tc=True)
+        b, wb, _ = _jump_states(S, (1 << 63) + 99, 0, monkeypatch, tc=False)
+        assert np.array_equal(a["rings"], b["rings"]), S
+        assert np.array_equal(wa[S - 1], O.u32_after_jump(int(seeds[S - 1]), 5 + (1 << 63) + 99, 48)), S
+
+
+def test_substreams_and_cut_calls_on_the_tensor_cores(monkeypatch):
+    """Doubling steps of 1024 and more pairs: 3000 substreams of one
+    sequence, and one call of 2^20 words cut into 16384 pieces of 64 words
+    (its prologue's last steps apply a power to 1024 .. 8192 pieces)."""
+    monkeypatch.setenv("XG_JUMP_TENSOR_CORES", "1")
+    seed = 0xC0FFEE
+    with Streams(3000) as st:
+        st.seed_substreams(seed, 20)
+        got = st.u32(32).cpu().numpy().view(np.uint32)
+    for i in (1, 1024, 2047, 2999):
+        assert np.array_equal(got[i], O.u32_after_jump(seed, i << 20, 32)), i
+    with Streams(2, seeds=[11, 12]) as st:
+        st.set_batch_split(64)
+        n = 1 << 20
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        st.batch([(0, "u32", n, out)])
+        torch.cuda.synchronize()
+        tail = st.u32(16, first=0, count=1).cpu().numpy().view(np.uint32)[0]
+    ref = O.Xorgens.param_set(0).seed(11).u32(n + 16)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref[:n])
+    assert np.array_equal(tail, ref[n:])
+
+
 def test_jump_composes_for_large_distances():
     seeds = W.seeds(4)
     a, b = (1 << 40) + 12345, (1 << 37) + 999

@@ -190,6 +190,22 @@ def test_jump_far_against_the_oracle(api):
                 assert np.array_equal(got[i], O.u64_after_jump(sd, J, 48, weyl=weyl)), (J, weyl, i)
 
 
+def test_jump_tensor_cores_against_the_table_kernel_and_the_oracle(api, monkeypatch):
+    """1500 64-bit streams: the tensor-core path equals the table kernel and
+    the oracle's jump."""
+    J = (1 << 50) + 777
+    seeds = list(range(900, 2400))
+    out = []
+    for tc in ("1", "0"):
+        monkeypatch.setenv("XG_JUMP_TENSOR_CORES", tc)
+        st = api.Streams64(len(seeds), seeds=seeds)
+        st.jump(J)
+        out.append(_u(st.u64(24)))
+    assert np.array_equal(out[0], out[1])
+    for i in (0, 1023, 1499):
+        assert np.array_equal(out[0][i], O.u64_after_jump(seeds[i], J, 24)), i
+
+
 def test_jump_composes_at_large_distances(api):
     """M^a M^b = M^(a+b) for distances up to 2^63, and the Weyl word
     advances by the distance times omega mod 2^64: jumping a then b gives
