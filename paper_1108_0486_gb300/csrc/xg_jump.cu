@@ -330,6 +330,81 @@ cudaError_t gf2_apply(int device, int family, int k, uint32_t* rings, uint32_t n
     return e;
 }
 
+// rings[dst[i]] = P rings[src[i]] for a matrix P in column form that is not
+// one of the cached powers; A_buf (16 MiB) receives its FP8 copy when the
+// tensor cores are used.
+static cudaError_t gf2_apply_explicit(int device, const uint64_t* P, uint8_t* A_buf, uint32_t* rings, uint32_t n,
+                                      const uint32_t* d_src, const uint32_t* d_dst, uint8_t* scratch, int sm_count,
+                                      cudaStream_t s)
+{
+    if (scratch && A_buf && gf2_use_tc(device, n)) {
+        cudaError_t e = gf2_tc_expand_matrix(P, A_buf, s);
+        if (e == cudaSuccess) e = gf2_tc_apply(device, A_buf, rings, d_src, n, rings, d_dst, scratch, s);
+        return e;
+    }
+    cudaError_t e = zero_rings(rings, d_dst, n, s);
+    if (e == cudaSuccess) e = launch_gf2_apply_pairs(P, rings, n, d_src, d_dst, sm_count, s);
+    return e;
+}
+
+size_t gf2_jump_scratch(int device, uint32_t n)
+{
+    // the product of powers (n > 4096) applies to 4096 columns, fewer than n
+    return gf2_apply_scratch(device, n);
+}
+
+cudaError_t gf2_jump_states(int device, int family, uint64_t words, uint32_t* rings, uint32_t n,
+                            const uint32_t* d_idx, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st,
+                            bool* result_hi)
+{
+    *st = XG_OK;
+    *result_hi = false;
+    const uint32_t* lo = d_idx;       // 0 .. n-1
+    const uint32_t* hi = d_idx + n;   // n .. 2n-1
+    const int nbits = __builtin_popcountll(words);
+    if (nbits < 2 || n <= (uint32_t)kGf2Bits) {
+        bool in_lo = true;
+        for (int k = 0; k < 64; ++k) {
+            if (!((words >> k) & 1)) continue;
+            cudaError_t e = gf2_apply(device, family, k, rings, n, in_lo ? lo : hi, in_lo ? hi : lo, scratch, sm_count, s, st);
+            if (e != cudaSuccess) return e;
+            in_lo = !in_lo;
+        }
+        *result_hi = !in_lo;
+        return cudaSuccess;
+    }
+    // multiply the powers first (they commute: all are powers of one
+    // matrix): b - 1 applications to the 4096 columns of a matrix in column
+    // form, then one to the states -- (b - 1) 4096 + n state applications
+    // instead of b n.  The identity list runs to 2n - 1 > 8191.
+    uint32_t* prod = nullptr;   // two 4096-column matrices (ping-pong)
+    uint8_t* abuf = nullptr;    // FP8 copy of the product (tensor cores)
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&prod), (size_t)2 * kBits * kR * 4, s);
+    if (e == cudaSuccess && scratch) e = cudaMallocAsync(reinterpret_cast<void**>(&abuf), (size_t)kGf2Bits * kGf2Bits, s);
+    bool p_lo = true, first_bit = true;
+    for (int k = 0; k < 64 && e == cudaSuccess; ++k) {
+        if (!((words >> k) & 1)) continue;
+        if (first_bit) {
+            const uint64_t* C = jump_matrix(device, family, k, s, st);
+            e = C ? cudaMemcpyAsync(prod, C, (size_t)kBits * kR * 4, cudaMemcpyDeviceToDevice, s)
+                  : cudaErrorMemoryAllocation;
+            first_bit = false;
+            continue;
+        }
+        e = gf2_apply(device, family, k, prod, kBits, p_lo ? lo : lo + kBits, p_lo ? lo + kBits : lo, scratch,
+                      sm_count, s, st);
+        p_lo = !p_lo;
+    }
+    if (e == cudaSuccess) {
+        const uint64_t* P = reinterpret_cast<const uint64_t*>(p_lo ? prod : prod + (size_t)kBits * kR);
+        e = gf2_apply_explicit(device, P, abuf, rings, n, lo, hi, scratch, sm_count, s);
+        *result_hi = true;
+    }
+    if (prod) cudaFreeAsync(prod, s);
+    if (abuf) cudaFreeAsync(abuf, s);
+    return e;
+}
+
 template <int NV>
 static cudaError_t launch_pairs(const uint64_t* C, uint32_t* rings, uint32_t n, const uint32_t* d_src,
                                 const uint32_t* d_dst, int sm_count, cudaStream_t s)
@@ -383,32 +458,30 @@ extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uin
     xg_status st = XG_OK;
     for (int k = 0; k <= top; ++k)
         if (((words >> k) & 1) && !jump_matrix(ctx->device, (int)ctx->param_set, k, s, &st)) return st;
-    // rings[0, n) hold the states, rings[n, 2n) receive each application
-    // (four-Russians table kernel, as in the batch prologue); the two halves
-    // swap roles after every set bit of words.
+    // rings[0, n) hold the states, rings[n, 2n) receive the results
     uint32_t* rings = nullptr;
     uint32_t* ids = nullptr;   // [0, 2n): stream ids for the gather, then 0..2n-1
     uint8_t* scratch = nullptr;  // tensor-core operand (when used)
-    const size_t sbytes = gf2_apply_scratch(ctx->device, nstreams);
+    const size_t sbytes = gf2_jump_scratch(ctx->device, nstreams);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)2 * nstreams * kR * 4, s);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)3 * nstreams * 4, s);
     if (e == cudaSuccess && sbytes) e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sbytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "xg_jump scratch");
+    if (e != cudaSuccess) {
+        for (void* p : {(void*)rings, (void*)ids})
+            if (p) cudaFreeAsync(p, s);
+        return cuda_fail(e, "xg_jump scratch");
+    }
     std::vector<uint32_t> h((size_t)3 * nstreams);
     for (uint32_t i = 0; i < nstreams; ++i) h[i] = first + i;
     for (uint32_t i = 0; i < 2 * nstreams; ++i) h[nstreams + i] = i;
-    const uint32_t* lo_idx = ids + nstreams;            // 0 .. n-1
-    const uint32_t* hi_idx = ids + 2 * (size_t)nstreams;  // n .. 2n-1
+    const uint32_t* lo_idx = ids + nstreams;            // 0 .. 2n-1
     e = cudaMemcpyAsync(ids, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_gather_rings(ctx->st, ids, nstreams, rings, nullptr, nullptr, 0, 0, s);
-    bool in_lo = true;
-    for (int k = 0; k <= top && e == cudaSuccess; ++k) {
-        if (!((words >> k) & 1)) continue;
-        const uint32_t* src = in_lo ? lo_idx : hi_idx;
-        const uint32_t* dst = in_lo ? hi_idx : lo_idx;
-        e = gf2_apply(ctx->device, (int)ctx->param_set, k, rings, nstreams, src, dst, scratch, ctx->sm_count, s, &st);
-        in_lo = !in_lo;
-    }
+    bool hi = false;
+    if (e == cudaSuccess)
+        e = gf2_jump_states(ctx->device, (int)ctx->param_set, words, rings, nstreams, lo_idx, scratch, ctx->sm_count, s,
+                            &st, &hi);
+    const bool in_lo = !hi;
     if (e == cudaSuccess) {
         const uint32_t* res = in_lo ? rings : rings + (size_t)nstreams * kR;
         scatter_rings_kernel<<<nstreams, 128, 0, s>>>(ctx->st, first, nstreams, res, words,

@@ -38,6 +38,16 @@ size_t gf2_apply_scratch(int device, uint32_t n);
 cudaError_t gf2_apply(int device, int family, int k, uint32_t* rings, uint32_t n, const uint32_t* d_src,
                       const uint32_t* d_dst, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st);
 
+// Advance n states by `words` positions: M^words applied to rings[0, n),
+// with rings[n, 2n) as the second buffer (*result_hi: the result ended there)
+// and d_idx the identity list 0 .. max(2n, 8192) - 1.  With several set bits
+// and n > 4096 the powers are multiplied first and the product applied once.
+// scratch: gf2_jump_scratch(device, n) bytes or null (table kernel only).
+size_t gf2_jump_scratch(int device, uint32_t n);
+cudaError_t gf2_jump_states(int device, int family, uint64_t words, uint32_t* rings, uint32_t n,
+                            const uint32_t* d_idx, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st,
+                            bool* result_hi);
+
 // rings[d_idx[i]] = 0 for n listed 128-word rings.
 cudaError_t zero_rings(uint32_t* rings, const uint32_t* d_idx, uint32_t n, cudaStream_t s);
 

@@ -397,13 +397,12 @@ xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t
     xg_status st = XG_OK;
     for (int k = 0; k <= top; ++k)
         if (((words >> k) & 1) && !xg::jump_matrix(c->device, xg::kJumpSetW64, k, s, &st)) return st;
-    // rings[0, n) hold the states, rings[n, 2n) receive each application;
-    // the halves swap roles after every set bit of words (the shared
-    // four-column table kernel works on 4096-bit states as 128 32-bit words)
+    // rings[0, n) hold the states, rings[n, 2n) the second buffer (the
+    // shared GF(2) kernels work on 4096-bit states as 128 32-bit words)
     uint64_t* rings = nullptr;
     uint32_t* ids = nullptr;   // 0 .. 2n-1
     uint8_t* tc_scratch = nullptr;  // tensor-core operand, when used
-    const size_t tc_bytes = xg::gf2_apply_scratch(c->device, nstreams);
+    const size_t tc_bytes = xg::gf2_jump_scratch(c->device, nstreams);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)2 * nstreams * xg64::kR * 8, s);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)2 * nstreams * 4, s);
     if (e == cudaSuccess && tc_bytes) e = cudaMallocAsync(reinterpret_cast<void**>(&tc_scratch), tc_bytes, s);
@@ -416,17 +415,13 @@ xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t
     for (uint32_t i = 0; i < 2 * nstreams; ++i) h[i] = i;
     uint32_t* rings32 = reinterpret_cast<uint32_t*>(rings);
     const uint32_t* lo_idx = ids;
-    const uint32_t* hi_idx = ids + nstreams;
     e = cudaMemcpyAsync(ids, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = xg64::launch_gather_rings(c->st, first, nstreams, rings, s);
-    bool in_lo = true;
-    for (int k = 0; k <= top && e == cudaSuccess; ++k) {
-        if (!((words >> k) & 1)) continue;
-        const uint32_t* src = in_lo ? lo_idx : hi_idx;
-        const uint32_t* dst = in_lo ? hi_idx : lo_idx;
-        e = xg::gf2_apply(c->device, xg::kJumpSetW64, k, rings32, nstreams, src, dst, tc_scratch, c->sm_count, s, &st);
-        in_lo = !in_lo;
-    }
+    bool hi = false;
+    if (e == cudaSuccess)
+        e = xg::gf2_jump_states(c->device, xg::kJumpSetW64, words, rings32, nstreams, lo_idx, tc_scratch, c->sm_count,
+                                s, &st, &hi);
+    const bool in_lo = !hi;
     if (e == cudaSuccess) {
         const uint64_t* res = in_lo ? rings : rings + (size_t)nstreams * xg64::kR;
         e = xg64::launch_scatter_rings(c->st, first, nstreams, res, words, c->weyl_on ? xg64::kOmega : 0, s);

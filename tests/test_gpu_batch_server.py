@@ -493,6 +493,20 @@ def test_jump_tensor_cores_against_the_table_kernel_and_the_oracle(ps, monkeypat
         assert np.array_equal(wa[i], O.u32_after_jump(int(seeds[i]), 5 + J, 48, param_set=ps)), i
 
 
+@pytest.mark.parametrize("tc", [True, False])
+def test_jump_many_streams_multiplies_the_powers_first(tc, monkeypatch):
+    """More than 4096 streams and several set bits: the powers are
+    multiplied first (b - 1 products of 4096-column matrices) and the
+    product applied once; equal to the oracle's jump, on the tensor cores
+    and on the table kernel."""
+    J = (1 << 44) + (1 << 30) + 777
+    S = 4500
+    a, wa, seeds = _jump_states(S, J, 0, monkeypatch, tc=tc)
+    for i in (0, 2222, 4096, S - 1):
+        assert np.array_equal(wa[i], O.u32_after_jump(int(seeds[i]), 5 + J, 48)), (tc, i)
+    assert np.array_equal(a["pos"], np.full(S, 5 + J, dtype=np.uint64))
+
+
 def test_jump_tensor_cores_small_and_partial_tiles(monkeypatch):
     """With the threshold lowered, 1, 37 and 300 states run on the tensor
     cores (one partly filled tile, and a second one nearly empty)."""

@@ -206,6 +206,20 @@ def test_jump_tensor_cores_against_the_table_kernel_and_the_oracle(api, monkeypa
         assert np.array_equal(out[0][i], O.u64_after_jump(seeds[i], J, 24)), i
 
 
+def test_jump_many_streams_multiplies_the_powers_first(api, monkeypatch):
+    """4200 64-bit streams and five set bits: the product of the powers
+    applied once, on both GF(2) paths, equal to the oracle's jump."""
+    J = (1 << 40) + (1 << 33) + 0b10101
+    seeds = list(range(5, 4205))
+    for tc in ("1", "0"):
+        monkeypatch.setenv("XG_JUMP_TENSOR_CORES", tc)
+        st = api.Streams64(len(seeds), seeds=seeds)
+        st.jump(J)
+        got = _u(st.u64(16))
+        for i in (0, 4100, 4199):
+            assert np.array_equal(got[i], O.u64_after_jump(seeds[i], J, 16)), (tc, i)
+
+
 def test_jump_composes_at_large_distances(api):
     """M^a M^b = M^(a+b) for distances up to 2^63, and the Weyl word
     advances by the distance times omega mod 2^64: jumping a then b gives
