@@ -12,14 +12,15 @@
 // K-major), followed by a parity epilogue that packs bits back into 32-bit
 // ring words.
 //
-// Kernel: one 128 x 256 output tile per CTA.  Warp 0 (one lane) streams
-// 128-byte-wide K blocks of A and B into a 4-stage shared-memory ring with
-// TMA (128B swizzle, mbarrier transaction counts); warp 1 (one lane) issues
-// tcgen05.mma (kind::f8f6f4, E4M3 x E4M3 -> F32, 128 x 256 x 32 each) into a
-// TMEM accumulator and frees each stage with tcgen05.commit; then all four
-// warps read the accumulator with tcgen05.ld (warp w owns TMEM lanes
-// 32w .. 32w+31 = output bits), take each count's parity and pack the 32
-// lanes' bits with a warp ballot: one ballot is one ring word of one state.
+// Kernel: persistent, one CTA per SM, 128 x 256 output tiles.  Warp 0 (one
+// lane) streams 128-byte-wide K blocks of A and B into a 4-stage
+// shared-memory ring with TMA (128B swizzle, mbarrier transaction counts);
+// warp 1 (one lane) issues tcgen05.mma (kind::f8f6f4, E4M3 x E4M3 -> F32,
+// 128 x 256 x 32 each) into one of two TMEM accumulators and frees each
+// stage with tcgen05.commit; four epilogue warps read the other accumulator
+// with tcgen05.ld (32 TMEM lanes = 32 output bits each), take each count's
+// parity and pack the 32 lanes' bits with a warp ballot: one ballot is one
+// ring word of one state.
 //
 // Every wait is bounded (2 s of %globaltimer); a wait that gives up records
 // a failure in a host-visible status word, the CTA waits (bounded) for its
@@ -45,6 +46,8 @@ constexpr int kABytes = kBM * kBK;        // 16 KiB
 constexpr int kBBytes = kBN * kBK;        // 32 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 /* barriers */ + 1024 /* alignment */;
+constexpr int kEpilogueWarps = 4;
+constexpr int kThreads = 32 * (2 + kEpilogueWarps);
 constexpr uint8_t kOneE4M3 = 0x38;        // 1.0 in FP8 E4M3
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
@@ -151,12 +154,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool failed(const volatile int* flag) { return *flag != 0; }
+
 // out[dst[s]] = C x_s for the n states of the B operand (rows >= n of B are
-// zero padding).  Grid: (4096 / kBM, n_pad / kBN), 128 threads.
-__global__ void __launch_bounds__(128, 1) gf2_tc_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                        const __grid_constant__ CUtensorMap tmB, uint32_t n,
-                                                        const uint32_t* __restrict__ dst, uint32_t* rings,
-                                                        uint32_t* status)
+// zero padding).  Persistent: CTA b takes tiles b, b + gridDim.x, ... of the
+// (4096 / kBM) x (n_pad / kBN) tiles, M fastest (consecutive tiles share a B
+// tile in L2).  192 threads: warp 0 = TMA producer, warp 1 = TMEM owner and
+// MMA issuer, warps 2-5 = epilogue (warp w reads TMEM lanes 32 (w mod 4) ..).
+// Two accumulators of kBN columns alternate, so that the epilogue of one
+// tile overlaps the MMAs of the next.
+__global__ void __launch_bounds__(kThreads, 1) gf2_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                              const __grid_constant__ CUtensorMap tmB, uint32_t n,
+                                                              uint32_t n_tiles, const uint32_t* __restrict__ dst,
+                                                              uint32_t* rings, uint32_t* status)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -164,26 +179,30 @@ __global__ void __launch_bounds__(128, 1) gf2_tc_kernel(const __grid_constant__ 
     uint8_t* sb = smem + kStages * kABytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(sb + kStages * kBBytes);
     uint64_t* empty = full + kStages;
-    uint64_t* accum = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-    __shared__ int s_failed;
+    uint64_t* tfull = empty + kStages;   // [2] accumulator ready (MMA commit)
+    uint64_t* tempty = tfull + 2;        // [2] accumulator drained (4 epilogue warps)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    __shared__ volatile int s_failed;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mt = blockIdx.x, nt = blockIdx.y;
-    const uint64_t deadline = global_ns() + kWaitLimitNs;
+    constexpr uint32_t kMTiles = kGf2Bits / kBM;
+    const uint32_t total = kMTiles * n_tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accum, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], kEpilogueWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_failed = 0;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"((uint32_t)kBN)
+                     "r"((uint32_t)(2 * kBN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -192,66 +211,92 @@ __global__ void __launch_bounds__(128, 1) gf2_tc_kernel(const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    int issued = 0;  // producer: K blocks whose copies were started
-    if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < kKBlocks; ++kb) {
-            const int s = kb % kStages;
-            if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) & 1) ^ 1, deadline)) {
-                s_failed = 1;
-                break;
+    uint32_t issued = 0;  // producer: K blocks whose copies were started
+    if (warp == 0) {
+        if (lane == 0) {
+            for (uint32_t t = blockIdx.x; t < total && !failed(&s_failed); t += gridDim.x) {
+                const int mt = (int)(t % kMTiles), nt = (int)(t / kMTiles);
+                for (int kb = 0; kb < kKBlocks; ++kb, ++issued) {
+                    const uint32_t s = issued % kStages, u = issued / kStages;
+                    if (issued >= (uint32_t)kStages && !mbar_wait(&empty[s], (u & 1) ^ 1, global_ns() + kWaitLimitNs)) {
+                        s_failed = 1;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], kStageBytes);
+                    tma_load_2d(sa + s * kABytes, &tmA, &full[s], kb * kBK, mt * kBM);
+                    tma_load_2d(sb + s * kBBytes, &tmB, &full[s], kb * kBK, nt * kBN);
+                }
             }
-            mbar_expect_tx(&full[s], kStageBytes);
-            tma_load_2d(sa + s * kABytes, &tmA, &full[s], kb * kBK, mt * kBM);
-            tma_load_2d(sb + s * kBBytes, &tmB, &full[s], kb * kBK, nt * kBN);
-            ++issued;
         }
-    } else if (warp == 1 && lane == 0) {
-        for (int kb = 0; kb < kKBlocks; ++kb) {
-            const int s = kb % kStages;
-            if (!mbar_wait(&full[s], (kb / kStages) & 1, deadline)) {
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0, lt = 0;
+            for (uint32_t t = blockIdx.x; t < total && !failed(&s_failed); t += gridDim.x, ++lt) {
+                const uint32_t acc = lt & 1, v = lt >> 1;
+                if (lt >= 2 && !mbar_wait(&tempty[acc], (v & 1) ^ 1, global_ns() + kWaitLimitNs)) {
+                    s_failed = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + acc * kBN;
+                for (int kb = 0; kb < kKBlocks; ++kb, ++it) {
+                    const uint32_t s = it % kStages, u = it / kStages;
+                    if (!mbar_wait(&full[s], u & 1, global_ns() + kWaitLimitNs)) {
+                        s_failed = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = smem_desc(sa + s * kABytes);
+                    const uint64_t bd = smem_desc(sb + s * kBBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 32; ++kk)  // K = 32 bytes per instruction: +2 in 16-byte units
+                        mma_f8(d, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[acc]);  // arrives once this tile's MMAs have completed
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue: this warp's 32 TMEM lanes = output bits 32 q .. 32 q + 31 of a tile
+        const uint32_t q = (uint32_t)(warp & 3);
+        uint32_t lt = 0;
+        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
+            const uint32_t acc = lt & 1, v = lt >> 1;
+            if (!mbar_wait(&tfull[acc], v & 1, global_ns() + kWaitLimitNs)) {
                 s_failed = 1;
                 break;
             }
             tc_fence_after();
-            const uint64_t ad = smem_desc(sa + s * kABytes);
-            const uint64_t bd = smem_desc(sb + s * kBBytes);
+            if (failed(&s_failed)) break;
+            const uint32_t mt = t % kMTiles, nt = t / kMTiles;
+            const uint32_t word = mt * (kBM / 32) + q;  // ring word of these 32 bits
+            for (int c = 0; c < kBN; c += 32) {
+                uint32_t vals[32];
+                tmem_ld32(tmem + ((q * 32) << 16) + acc * kBN + (uint32_t)c, vals);
+                uint32_t mine = 0;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 32; ++kk)  // K = 32 bytes per instruction: +2 in 16-byte units
-                mma_f8(tmem, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
-            mma_commit(&empty[s]);
-        }
-        mma_commit(accum);  // arrives once every MMA issued above has completed
-    }
-    __syncwarp();
-
-    // epilogue: warp w holds output bits 32w .. 32w+31 of this tile
-    const bool ready = mbar_wait(accum, 0, deadline);
-    tc_fence_after();
-    if (ready && !s_failed) {
-        const uint32_t word = (uint32_t)(mt * (kBM / 32) + warp);  // ring word of these 32 bits
-        for (int c = 0; c < kBN; c += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            uint32_t mine = 0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                // the count is an integer <= 4096: adding 2^23 puts its parity in the last bit
-                const uint32_t bit = __float_as_uint(__uint_as_float(v[j]) + 8388608.0f) & 1u;
-                const uint32_t b = __ballot_sync(0xFFFFFFFFu, bit);
-                if (lane == j) mine = b;
+                for (int j = 0; j < 32; ++j) {
+                    // the count is an integer <= 4096: adding 2^23 puts its parity in the last bit
+                    const uint32_t bit = __float_as_uint(__uint_as_float(vals[j]) + 8388608.0f) & 1u;
+                    const uint32_t b = __ballot_sync(0xFFFFFFFFu, bit);
+                    if (lane == j) mine = b;
+                }
+                const uint32_t st = nt * kBN + (uint32_t)c + (uint32_t)lane;
+                if (st < n) rings[(size_t)dst[st] * kGf2Words + word] = mine;
             }
-            const uint32_t s = (uint32_t)(nt * kBN + c + lane);
-            if (s < n) rings[(size_t)dst[s] * kGf2Words + word] = mine;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
         }
-    } else if (threadIdx.x == 0) {
-        s_failed = 1;
     }
     tc_fence_before();
     __syncthreads();
-    if (s_failed) {
+    if (failed(&s_failed)) {
         if (warp == 0 && lane == 0) {
             // the copies of the last (at most kStages) started K blocks may still be in flight
-            for (int kb = issued > kStages ? issued - kStages : 0; kb < issued; ++kb)
+            for (uint32_t kb = issued > (uint32_t)kStages ? issued - kStages : 0u; kb < issued; ++kb)
                 (void)mbar_wait(&full[kb % kStages], (kb / kStages) & 1, global_ns() + kWaitLimitNs);
         }
         if (threadIdx.x == 0) {
@@ -260,9 +305,9 @@ __global__ void __launch_bounds__(128, 1) gf2_tc_kernel(const __grid_constant__ 
         }
         __syncthreads();
     }
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kBN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * kBN))
                      : "memory");
     }
 }
@@ -408,8 +453,12 @@ cudaError_t gf2_tc_apply(int device, const uint8_t* A, const uint32_t* rings_in,
     expand_states_kernel<<<(unsigned)((words + 255) / 256), 256, 0, s>>>(rings_in, src, n, n_pad, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    gf2_tc_kernel<<<dim3(kGf2Bits / kBM, n_pad / kBN), 128, kSmemBytes, s>>>(ma, mb, n, dst, rings_out,
-                                                                               g_status_dev);
+    const uint32_t n_tiles = n_pad / kBN;
+    const uint32_t tiles = (kGf2Bits / kBM) * n_tiles;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 1;
+    const unsigned grid = (unsigned)std::min<uint32_t>(tiles, (uint32_t)sms);
+    gf2_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(ma, mb, n, n_tiles, dst, rings_out, g_status_dev);
     return cudaGetLastError();
 }
 
