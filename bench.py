@@ -55,6 +55,16 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _fp8_peak():
+    """Dense FP8 tensor peak: the measured bf16 GEMM rate times the nominal
+    FP8 / bf16 ratio of 2, else the nominal 4.5 PFLOP/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return 2.0 * float(json.load(f)["bf16_tflops"]), "measured bf16 x 2"
+    except Exception:
+        return 4500.0, "nominal"
+
+
 def _record(name):
     """A profiles/ record (key value lines) taken with ncu, if it was taken
     on the current kernel sources (else None)."""
@@ -556,8 +566,24 @@ def extra_rows(st, stream, torch, peak, sm_mhz=None):
     # i.e. 8 applications of a 4096 x 4096 GF(2) matrix per stream
     J = (1 << 40) + (1 << 20) + 12345
     ms = _time(lambda: st.jump(J), stream, torch)
-    rows["jump_16384_streams"] = {"words": J, "set_bits": bin(J).count("1"), "ms": ms,
-                                  "us_per_stream_application": ms * 1e3 / (STREAMS * bin(J).count("1"))}
+    bits = bin(J).count("1")
+    # the powers are multiplied first ((bits - 1) applications to the 4096
+    # columns of a matrix), then the product is applied to the streams; each
+    # application of a 4096 x 4096 GF(2) matrix to one state is 2 * 4096^2
+    # FP8 tensor operations on the tensor-core path
+    apps = (bits - 1) * 4096 + STREAMS
+    tflops = 2 * 4096 ** 2 * apps / (ms / 1e3) / 1e12
+    fp8_peak = _fp8_peak()
+    os.environ["XG_JUMP_TENSOR_CORES"] = "0"
+    try:
+        ms_table = _time(lambda: st.jump(J), stream, torch)
+    finally:
+        del os.environ["XG_JUMP_TENSOR_CORES"]
+    rows["jump_16384_streams"] = {"words": J, "set_bits": bits, "ms": ms, "state_applications": apps,
+                                  "tensor_tflops": tflops, "fp8_peak_tflops": fp8_peak[0],
+                                  "fp8_peak_source": fp8_peak[1], "frac_of_fp8_peak": tflops / fp8_peak[0],
+                                  "ms_table_kernel": ms_table,
+                                  "note": "whole call: gather, FP8 expansion, tensor-core GEMMs, scatter"}
     # 16384 disjoint substreams of one sequence, 2^40 words apart (14 doubling
     # steps, one matrix application per stream); the streams are re-seeded
     # with their own seeds afterwards
