@@ -1021,6 +1021,11 @@ def profile_kernel(args):
         # one matrix application per stream per call (2^20 has one set bit)
         st = Streams(STREAMS, seeds=W.seeds(STREAMS), stream=stream)
         out["ms"] = _time(lambda: st.jump(1 << 20), stream, torch, reps=args.steps, warm=args.warmup)
+    elif args.kernel == "jump8":
+        # the bench row's jump: 2^40 + 2^20 + 12345 words, 8 set bits
+        st = Streams(STREAMS, seeds=W.seeds(STREAMS), stream=stream)
+        J = (1 << 40) + (1 << 20) + 12345
+        out["ms"] = _time(lambda: st.jump(J), stream, torch, reps=args.steps, warm=args.warmup)
     elif args.kernel == "batch":
         items = [it for it in W.batched_uneven() if it.count <= n] if args.n_per else W.batched_uneven()
         st = Streams(4096, seeds=W.seeds(4096), stream=stream)
@@ -1044,7 +1049,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window of the serving row (10 s: about 200K requests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["u32", "uniform", "normal", "normal_sum", "batch", "w64_uniform", "jump"],
+    ap.add_argument("--kernel", default=None, choices=["u32", "uniform", "normal", "normal_sum", "batch", "w64_uniform", "jump", "jump8"],
                     help="time one kernel's workload alone (profiling case; not a bench line)")
     ap.add_argument("--n-per", type=int, default=None,
                     help="override words per stream (profiling of a smaller case; not a bench line)")
