@@ -563,6 +563,18 @@ def extra_rows(st, stream, torch, peak, sm_mhz=None):
     rows["normal_sum_fused"] = {"rn_s": rn / (ms / 1e3), "ms": ms, "hbm_bytes_written": STREAMS * 4}
     ms = _time(lambda: st.u32(n, out=buf.view(torch.int32)), stream, torch)
     rows["u32"] = {"rn_s": rn / (ms / 1e3), "ms": ms, "hbm_frac": rn * 4 / (ms / 1e3) / 1e9 / peak}
+    # the paper's parameter set (128,65,15,14,12,17) on the same kernels,
+    # its own autotuned launch shapes: 2^16 u32 and 2^16 uniforms per stream
+    from paper_1108_0486_gb300 import Streams as _S
+    sp = _S(STREAMS, param_set=1, seeds=W.seeds(STREAMS), stream=stream)
+    paper = {"param_set": "(128,65,15,14,12,17)", "launch": {}}
+    for kind in ("u32", "uniform"):
+        paper["launch"][kind] = sp.autotune(kind, n)
+        view = buf.view(torch.int32) if kind == "u32" else buf
+        msk = _time(lambda: sp.generate(kind, n, out=view), stream, torch)
+        paper[kind] = {"ms": msk, "rn_s": rn / (msk / 1e3), "hbm_frac": rn * 4 / (msk / 1e3) / 1e9 / peak}
+    sp.close()
+    rows["paper_parameter_set"] = paper
     del buf
     # jump-ahead of every stream: J = 2^40 + 2^20 + 12345 words, 8 set bits,
     # i.e. 8 applications of a 4096 x 4096 GF(2) matrix per stream
