@@ -347,22 +347,35 @@ static cudaError_t gf2_apply_explicit(int device, const uint64_t* P, uint8_t* A_
     return e;
 }
 
-size_t gf2_jump_scratch(int device, uint32_t n)
+static bool jump_combines(uint64_t words, uint32_t n)
 {
-    // the product of powers (n > 4096) applies to 4096 columns, fewer than n
-    return gf2_apply_scratch(device, n);
+    return __builtin_popcountll(words) >= 2 && n > (uint32_t)kGf2Bits;
+}
+
+size_t gf2_jump_work_bytes(int device, uint32_t n, uint64_t words)
+{
+    // the tensor-core operand (the product of powers, n > 4096, applies to
+    // 4096 columns, fewer than n), then the product matrix pair and its FP8
+    // copy when the powers are multiplied first
+    size_t b = (gf2_apply_scratch(device, n) + 255) / 256 * 256;
+    if (jump_combines(words, n)) {
+        b += (size_t)2 * kBits * kR * 4;
+        if (gf2_use_tc(device, n)) b += (size_t)kGf2Bits * kGf2Bits;
+    }
+    return b;
 }
 
 cudaError_t gf2_jump_states(int device, int family, uint64_t words, uint32_t* rings, uint32_t n,
-                            const uint32_t* d_idx, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st,
+                            const uint32_t* d_idx, uint8_t* work, int sm_count, cudaStream_t s, xg_status* st,
                             bool* result_hi)
 {
     *st = XG_OK;
     *result_hi = false;
     const uint32_t* lo = d_idx;       // 0 .. n-1
     const uint32_t* hi = d_idx + n;   // n .. 2n-1
-    const int nbits = __builtin_popcountll(words);
-    if (nbits < 2 || n <= (uint32_t)kGf2Bits) {
+    const size_t sbytes = gf2_apply_scratch(device, n);
+    uint8_t* scratch = sbytes ? work : nullptr;
+    if (!jump_combines(words, n)) {
         bool in_lo = true;
         for (int k = 0; k < 64; ++k) {
             if (!((words >> k) & 1)) continue;
@@ -377,10 +390,10 @@ cudaError_t gf2_jump_states(int device, int family, uint64_t words, uint32_t* ri
     // matrix): b - 1 applications to the 4096 columns of a matrix in column
     // form, then one to the states -- (b - 1) 4096 + n state applications
     // instead of b n.  The identity list runs to 2n - 1 > 8191.
-    uint32_t* prod = nullptr;   // two 4096-column matrices (ping-pong)
-    uint8_t* abuf = nullptr;    // FP8 copy of the product (tensor cores)
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&prod), (size_t)2 * kBits * kR * 4, s);
-    if (e == cudaSuccess && scratch) e = cudaMallocAsync(reinterpret_cast<void**>(&abuf), (size_t)kGf2Bits * kGf2Bits, s);
+    uint8_t* w = work + (sbytes + 255) / 256 * 256;
+    uint32_t* prod = reinterpret_cast<uint32_t*>(w);   // two 4096-column matrices (ping-pong)
+    uint8_t* abuf = scratch ? w + (size_t)2 * kBits * kR * 4 : nullptr;  // FP8 copy of the product
+    cudaError_t e = cudaSuccess;
     bool p_lo = true, first_bit = true;
     for (int k = 0; k < 64 && e == cudaSuccess; ++k) {
         if (!((words >> k) & 1)) continue;
@@ -400,9 +413,22 @@ cudaError_t gf2_jump_states(int device, int family, uint64_t words, uint32_t* ri
         e = gf2_apply_explicit(device, P, abuf, rings, n, lo, hi, scratch, sm_count, s);
         *result_hi = true;
     }
-    if (prod) cudaFreeAsync(prod, s);
-    if (abuf) cudaFreeAsync(abuf, s);
     return e;
+}
+
+// ids[i] = first + i for i < n, then ids[n + j] = j for j < 2n.
+__global__ void jump_index_kernel(uint32_t* __restrict__ ids, uint32_t n, uint32_t first)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ids[i] = first + (uint32_t)i;
+    else if (i < (uint64_t)3 * n) ids[i] = (uint32_t)(i - n);
+}
+
+cudaError_t launch_jump_index(uint32_t* ids, uint32_t n, uint32_t first, cudaStream_t s)
+{
+    const uint64_t total = (uint64_t)3 * n;
+    jump_index_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ids, n, first);
+    return cudaGetLastError();
 }
 
 template <int NV>
@@ -458,29 +484,24 @@ extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uin
     xg_status st = XG_OK;
     for (int k = 0; k <= top; ++k)
         if (((words >> k) & 1) && !jump_matrix(ctx->device, (int)ctx->param_set, k, s, &st)) return st;
-    // rings[0, n) hold the states, rings[n, 2n) receive the results
-    uint32_t* rings = nullptr;
-    uint32_t* ids = nullptr;   // [0, 2n): stream ids for the gather, then 0..2n-1
-    uint8_t* scratch = nullptr;  // tensor-core operand (when used)
-    const size_t sbytes = gf2_jump_scratch(ctx->device, nstreams);
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)2 * nstreams * kR * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)3 * nstreams * 4, s);
-    if (e == cudaSuccess && sbytes) e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sbytes, s);
-    if (e != cudaSuccess) {
-        for (void* p : {(void*)rings, (void*)ids})
-            if (p) cudaFreeAsync(p, s);
-        return cuda_fail(e, "xg_jump scratch");
-    }
-    std::vector<uint32_t> h((size_t)3 * nstreams);
-    for (uint32_t i = 0; i < nstreams; ++i) h[i] = first + i;
-    for (uint32_t i = 0; i < 2 * nstreams; ++i) h[nstreams + i] = i;
-    const uint32_t* lo_idx = ids + nstreams;            // 0 .. 2n-1
-    e = cudaMemcpyAsync(ids, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
+    // workspace kept in the context (grow-only): rings[0, n) hold the
+    // states, rings[n, 2n) receive the results; index lists (stream ids for
+    // the gather, then 0 .. 2n-1); the jump's own work area
+    const size_t rings_bytes = (size_t)2 * nstreams * kR * 4;
+    const size_t ids_off = rings_bytes;
+    const size_t work_off = (ids_off + (size_t)3 * nstreams * 4 + 255) / 256 * 256;
+    const size_t wbytes = gf2_jump_work_bytes(ctx->device, nstreams, words);
+    if (xg_status g = ctx->ensure_jump_ws(work_off + wbytes)) return g;
+    char* ws = static_cast<char*>(ctx->jump_ws);
+    uint32_t* rings = reinterpret_cast<uint32_t*>(ws);
+    uint32_t* ids = reinterpret_cast<uint32_t*>(ws + ids_off);
+    const uint32_t* lo_idx = ids + nstreams;  // 0 .. 2n-1
+    cudaError_t e = launch_jump_index(ids, nstreams, first, s);
     if (e == cudaSuccess) e = launch_gather_rings(ctx->st, ids, nstreams, rings, nullptr, nullptr, 0, 0, s);
     bool hi = false;
     if (e == cudaSuccess)
-        e = gf2_jump_states(ctx->device, (int)ctx->param_set, words, rings, nstreams, lo_idx, scratch, ctx->sm_count, s,
-                            &st, &hi);
+        e = gf2_jump_states(ctx->device, (int)ctx->param_set, words, rings, nstreams, lo_idx,
+                            reinterpret_cast<uint8_t*>(ws + work_off), ctx->sm_count, s, &st, &hi);
     const bool in_lo = !hi;
     if (e == cudaSuccess) {
         const uint32_t* res = in_lo ? rings : rings + (size_t)nstreams * kR;
@@ -488,10 +509,8 @@ extern "C" xg_status xg_jump(xg_ctx* ctx, uint32_t first, uint32_t nstreams, uin
                                                       ctx->weyl_on ? 0x9E3779B9u : 0u);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
-    cudaFreeAsync(rings, s);
-    cudaFreeAsync(ids, s);
-    if (scratch) cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const size_t sbytes = gf2_apply_scratch(ctx->device, nstreams);
     if (st != XG_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "xg_jump");
     if (sbytes && gf2_tc_take_failure())

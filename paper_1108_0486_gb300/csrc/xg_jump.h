@@ -42,11 +42,16 @@ cudaError_t gf2_apply(int device, int family, int k, uint32_t* rings, uint32_t n
 // with rings[n, 2n) as the second buffer (*result_hi: the result ended there)
 // and d_idx the identity list 0 .. max(2n, 8192) - 1.  With several set bits
 // and n > 4096 the powers are multiplied first and the product applied once.
-// scratch: gf2_jump_scratch(device, n) bytes or null (table kernel only).
-size_t gf2_jump_scratch(int device, uint32_t n);
+// work: gf2_jump_work_bytes(device, n, words) bytes of device memory,
+// 256-byte aligned (the tensor-core operand, and the product matrices when
+// the powers are multiplied first).
+size_t gf2_jump_work_bytes(int device, uint32_t n, uint64_t words);
 cudaError_t gf2_jump_states(int device, int family, uint64_t words, uint32_t* rings, uint32_t n,
-                            const uint32_t* d_idx, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st,
+                            const uint32_t* d_idx, uint8_t* work, int sm_count, cudaStream_t s, xg_status* st,
                             bool* result_hi);
+
+// ids[i] = first + i for i < n, then ids[n + j] = j for j < 2n (3n entries).
+cudaError_t launch_jump_index(uint32_t* ids, uint32_t n, uint32_t first, cudaStream_t s);
 
 // rings[d_idx[i]] = 0 for n listed 128-word rings.
 cudaError_t zero_rings(uint32_t* rings, const uint32_t* d_idx, uint32_t n, cudaStream_t s);

@@ -75,6 +75,23 @@ int xg_ctx::pick_block(int kind, int c) const
     return (cfg[t] == c && blk[t] > 0) ? blk[t] : block[c];
 }
 
+xg_status xg_ctx::ensure_jump_ws(size_t bytes)
+{
+    if (jump_ws_bytes >= bytes) return XG_OK;
+    if (jump_ws) {
+        cudaStreamSynchronize(stream);
+        cudaFree(jump_ws);
+    }
+    jump_ws = nullptr;
+    jump_ws_bytes = 0;
+    if (cudaMalloc(&jump_ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return xg::fail(XG_ENOMEM, "cudaMalloc(jump workspace, %zu bytes) failed", bytes);
+    }
+    jump_ws_bytes = bytes;
+    return XG_OK;
+}
+
 xg_status xg_ctx::ensure_staging(size_t bytes)
 {
     if (staging_bytes >= bytes) return XG_OK;
@@ -308,6 +325,7 @@ xg_status xg_destroy(xg_ctx* ctx)
         if (c->ev_copy[b]) cudaEventDestroy(c->ev_copy[b]);
         if (c->staging[b]) cudaFree(c->staging[b]);
     }
+    if (c->jump_ws) cudaFree(c->jump_ws);
     if (c->state_mem) cudaFree(c->state_mem);
     delete c;
     return XG_OK;

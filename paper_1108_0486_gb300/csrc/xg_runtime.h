@@ -49,9 +49,14 @@ struct xg_ctx {
     // xg_autotune_batch
     uint8_t batch_shape[3] = {xg::kShapeChain, xg::kShapeChain, xg::kShapeChain};
 
+    // xg_jump's workspace (grow-only, freed by xg_destroy)
+    void* jump_ws = nullptr;
+    size_t jump_ws_bytes = 0;
+
     int pick_cfg(int kind, uint32_t nstreams) const;
     int pick_block(int kind, int cfg) const;
     xg_status ensure_staging(size_t bytes);
+    xg_status ensure_jump_ws(size_t bytes);
     void shutdown_server();
 };
 

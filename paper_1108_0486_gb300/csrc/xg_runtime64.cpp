@@ -397,39 +397,34 @@ xg_status xg_w64_jump(xg_w64_ctx* c, uint32_t first, uint32_t nstreams, uint64_t
     xg_status st = XG_OK;
     for (int k = 0; k <= top; ++k)
         if (((words >> k) & 1) && !xg::jump_matrix(c->device, xg::kJumpSetW64, k, s, &st)) return st;
-    // rings[0, n) hold the states, rings[n, 2n) the second buffer (the
-    // shared GF(2) kernels work on 4096-bit states as 128 32-bit words)
-    uint64_t* rings = nullptr;
-    uint32_t* ids = nullptr;   // 0 .. 2n-1
-    uint8_t* tc_scratch = nullptr;  // tensor-core operand, when used
-    const size_t tc_bytes = xg::gf2_jump_scratch(c->device, nstreams);
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)2 * nstreams * xg64::kR * 8, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ids), (size_t)2 * nstreams * 4, s);
-    if (e == cudaSuccess && tc_bytes) e = cudaMallocAsync(reinterpret_cast<void**>(&tc_scratch), tc_bytes, s);
-    if (e != cudaSuccess) {
-        if (rings) cudaFreeAsync(rings, s);
-        if (ids) cudaFreeAsync(ids, s);
-        return cuda_fail(e, "xg_w64_jump scratch");
-    }
-    std::vector<uint32_t> h((size_t)2 * nstreams);
-    for (uint32_t i = 0; i < 2 * nstreams; ++i) h[i] = i;
-    uint32_t* rings32 = reinterpret_cast<uint32_t*>(rings);
-    const uint32_t* lo_idx = ids;
-    e = cudaMemcpyAsync(ids, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
+    // one allocation: rings[0, n) hold the states, rings[n, 2n) the second
+    // buffer (the shared GF(2) kernels work on 4096-bit states as 128 32-bit
+    // words); index lists (0 .. n-1, then 0 .. 2n-1, built on the device);
+    // the jump's work area
+    const size_t rings_bytes = (size_t)2 * nstreams * xg64::kR * 8;
+    const size_t work_off = (rings_bytes + (size_t)3 * nstreams * 4 + 255) / 256 * 256;
+    const size_t wbytes = xg::gf2_jump_work_bytes(c->device, nstreams, words);
+    const size_t tc_bytes = xg::gf2_apply_scratch(c->device, nstreams);
+    char* ws = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), work_off + wbytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "xg_w64_jump scratch");
+    uint64_t* rings = reinterpret_cast<uint64_t*>(ws);
+    uint32_t* rings32 = reinterpret_cast<uint32_t*>(ws);
+    uint32_t* ids = reinterpret_cast<uint32_t*>(ws + rings_bytes);
+    const uint32_t* lo_idx = ids + nstreams;  // 0 .. 2n-1
+    e = xg::launch_jump_index(ids, nstreams, 0u, s);
     if (e == cudaSuccess) e = xg64::launch_gather_rings(c->st, first, nstreams, rings, s);
     bool hi = false;
     if (e == cudaSuccess)
-        e = xg::gf2_jump_states(c->device, xg::kJumpSetW64, words, rings32, nstreams, lo_idx, tc_scratch, c->sm_count,
-                                s, &st, &hi);
+        e = xg::gf2_jump_states(c->device, xg::kJumpSetW64, words, rings32, nstreams, lo_idx,
+                                reinterpret_cast<uint8_t*>(ws + work_off), c->sm_count, s, &st, &hi);
     const bool in_lo = !hi;
     if (e == cudaSuccess) {
         const uint64_t* res = in_lo ? rings : rings + (size_t)nstreams * xg64::kR;
         e = xg64::launch_scatter_rings(c->st, first, nstreams, res, words, c->weyl_on ? xg64::kOmega : 0, s);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
-    cudaFreeAsync(rings, s);
-    cudaFreeAsync(ids, s);
-    if (tc_scratch) cudaFreeAsync(tc_scratch, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(ws, s);
     if (st != XG_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "xg_w64_jump");
     if (tc_bytes && xg::gf2_tc_take_failure())
