@@ -135,8 +135,13 @@ static void plan_order(BatchPlan& plan)
 {
     constexpr uint32_t kKeys = 59u << 6;   // cost_key < 58 * 64 + 64
     const size_t nh = plan.heads.size();
-    std::vector<uint32_t> start(kKeys + 1, 0u);
-    std::vector<uint32_t> key(nh);
+    // buffers kept in the plan between calls (no allocation once grown)
+    std::vector<uint32_t>& start = plan.sort_start;
+    std::vector<uint32_t>& key = plan.sort_key;
+    std::vector<uint32_t>& sorted = plan.sort_heads;
+    std::vector<uint64_t>& cost = plan.sort_cost;
+    start.assign(kKeys + 1, 0u);
+    key.resize(nh);
     for (size_t k = 0; k < nh; ++k) {
         key[k] = cost_key(plan.chain_words[k]);
         ++start[kKeys - 1 - key[k]];   // descending
@@ -147,8 +152,8 @@ static void plan_order(BatchPlan& plan)
         start[b] = acc;
         acc += v;
     }
-    std::vector<uint32_t> sorted(nh);
-    std::vector<uint64_t> cost(nh);
+    sorted.resize(nh);
+    cost.resize(nh);
     for (size_t k = 0; k < nh; ++k) {
         const uint32_t pos = start[kKeys - 1 - key[k]]++;
         sorted[pos] = plan.heads[k];

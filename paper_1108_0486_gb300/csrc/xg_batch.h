@@ -37,6 +37,9 @@ struct BatchPlan {
     int split_log2 = 0;                  // piece length 2^split_log2 (when pieces exist)
     // dense per-stream scratch, all zero between calls
     std::vector<uint32_t> items_of_stream, last_unit, chain_of;
+    // the head ordering's buffers, reused between calls
+    std::vector<uint32_t> sort_start, sort_key, sort_heads;
+    std::vector<uint64_t> sort_cost;
 };
 
 // Plan a batch.  piece_len: 0 = cut nothing, else a power of two; calls alone
