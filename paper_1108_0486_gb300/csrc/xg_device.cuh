@@ -154,6 +154,112 @@ __device__ __forceinline__ void normal_pair(uint32_t o1, uint32_t o2, float& z1,
 }
 
 // ---------------------------------------------------------------------------
+// Two pairs at once with the packed FP32x2 instructions (fma/mul/add.rn.f32x2):
+// every floating-point step of normal_pair applied to pair A in the low half
+// and pair B in the high half of a 64-bit register pair.  Each half is
+// rounded exactly as the scalar instruction rounds it, so the results are
+// the same bits as two calls of normal_pair; the integer steps, the
+// conversions, the reciprocal square root and the quadrant selection stay
+// scalar.  If either pair takes the FP64 tail, both go through normal_pair.
+using f32x2 = unsigned long long;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo2(f32x2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi2(f32x2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 dup2(float v) { return pk2(v, v); }
+
+__device__ __forceinline__ void normal_pair2(uint32_t o1a, uint32_t o2a, uint32_t o1b, uint32_t o2b, float& z1a,
+                                             float& z2a, float& z1b, float& z2b)
+{
+    const uint32_t m1a = (o1a >> 8) + 1u, m1b = (o1b >> 8) + 1u;
+    if (m1a <= 62u || m1b <= 62u) {
+        normal_pair(o1a, o2a, z1a, z2a);
+        normal_pair(o1b, o2b, z1b, z2b);
+        return;
+    }
+    // radius: the exponent split of neg2ln_u1, per pair
+    const int da = __float_as_int(__uint2float_rn(m1a)) - (0x3F3504F3 + (24 << 23));
+    const int db = __float_as_int(__uint2float_rn(m1b)) - (0x3F3504F3 + (24 << 23));
+    const f32x2 f = pk2(__int_as_float((da & 0x7FFFFF) + 0x3F3504F3), __int_as_float((db & 0x7FFFFF) + 0x3F3504F3));
+    const f32x2 t = add2(f, dup2(-1.0f));                          // exact
+    f32x2 q = dup2(kLogQ[8]);
+#pragma unroll
+    for (int i = 7; i >= 0; --i) q = fma2(q, t, dup2(kLogQ[i]));
+    const f32x2 lnf = fma2(mul2(t, t), q, t);
+    const f32x2 e = pk2(__int2float_rn(da >> 23), __int2float_rn(db >> 23));
+    const f32x2 L = fma2(e, dup2(kNeg2Ln2Hi), fma2(e, dup2(kNeg2Ln2Lo), mul2(dup2(-2.0f), lnf)));
+    // R = sqrt(L): sqrt_refined on both halves
+    float ya, yb;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ya) : "f"(fmaxf(lo2(L), 0x1p-100f)));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yb) : "f"(fmaxf(hi2(L), 0x1p-100f)));
+    const f32x2 y = pk2(ya, yb);
+    const f32x2 r0 = mul2(L, y);
+    const f32x2 dd = fma2(mul2(r0, dup2(-1.0f)), r0, L);         // -r0 exact
+    const f32x2 R = fma2(dd, mul2(dup2(0.5f), y), r0);
+    // angle: normal_pair's exact reduction, per pair for the integer parts
+    const uint32_t mma = (o2a >> 8) + (1u << 21), mmb = (o2b >> 8) + (1u << 21);
+    const f32x2 xq = add2(pk2(__uint_as_float((mma & 0x3FFFFFu) | 0x3F800000u),
+                              __uint_as_float((mmb & 0x3FFFFFu) | 0x3F800000u)),
+                          dup2(-1.25f));
+    const f32x2 yq = mul2(xq, xq);
+    f32x2 sp = dup2(kSinS[3] * 16384.0f);
+    sp = fma2(sp, yq, dup2(kSinS[2] * 1024.0f));
+    sp = fma2(sp, yq, dup2(kSinS[1] * 64.0f));
+    const f32x2 sv = fma2(xq, dup2(kSinS[0] * 4.0f), fma2(xq, dup2(kSinS0Lo * 4.0f), mul2(mul2(xq, yq), sp)));
+    f32x2 cp = dup2(kCosC[3] * 65536.0f);
+    cp = fma2(cp, yq, dup2(kCosC[2] * 4096.0f));
+    cp = fma2(cp, yq, dup2(kCosC[1] * 256.0f));
+    cp = fma2(cp, yq, dup2(kCosC[0] * 16.0f));
+    const f32x2 cv = fma2(cp, yq, dup2(1.0f));
+    // quadrants (scalar), then the products with R for both pairs at once
+    const float sa = lo2(sv), sb = hi2(sv), ca = lo2(cv), cb = hi2(cv);
+    const bool odda = (mma >> 22) & 1u, oddb = (mmb >> 22) & 1u;
+    const float csa = odda ? sa : ca, sna = odda ? ca : sa;
+    const float csb = oddb ? sb : cb, snb = oddb ? cb : sb;
+    const uint32_t cfa = ((mma + (1u << 22)) << 8) & 0x80000000u, sfa = (mma << 8) & 0x80000000u;
+    const uint32_t cfb = ((mmb + (1u << 22)) << 8) & 0x80000000u, sfb = (mmb << 8) & 0x80000000u;
+    const f32x2 z1 = mul2(R, pk2(__uint_as_float(__float_as_uint(csa) ^ cfa), __uint_as_float(__float_as_uint(csb) ^ cfb)));
+    const f32x2 z2 = mul2(R, pk2(__uint_as_float(__float_as_uint(sna) ^ sfa), __uint_as_float(__float_as_uint(snb) ^ sfb)));
+    z1a = lo2(z1);
+    z1b = hi2(z1);
+    z2a = lo2(z2);
+    z2b = hi2(z2);
+}
+
+// ---------------------------------------------------------------------------
 // The round engine of one generator group.
 template <class P, int TPG, int WPL>
 struct Engine {

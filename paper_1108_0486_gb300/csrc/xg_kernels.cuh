@@ -129,11 +129,22 @@ __device__ __forceinline__ int drive(E& eng, uint64_t nr, Emit& emit,
     uint64_t r = 0;
     if constexpr (UNROLL2) {
         for (; r + 2 * E::NROWS < nr; r += 2 * E::NROWS) {
-            static_for<0, 2 * E::NROWS>([&](auto kc) {
-                constexpr int K = decltype(kc)::value % E::NROWS;
-                eng.template round<K>();
-                emit.template full<K>(eng);
-            });
+            if constexpr (Emit::kPairRounds) {
+                // two-row ring: after rounds 0 and 1 the rows hold both
+                // rounds' words (round 1 writes only row 1), whose normal
+                // pairs then go through the packed transform together
+                static_for<0, 2>([&](auto) {
+                    eng.template round<0>();
+                    eng.template round<1>();
+                    emit.full_rounds01(eng);
+                });
+            } else {
+                static_for<0, 2 * E::NROWS>([&](auto kc) {
+                    constexpr int K = decltype(kc)::value % E::NROWS;
+                    eng.template round<K>();
+                    emit.template full<K>(eng);
+                });
+            }
         }
     }
     while (r + E::NROWS < nr) {
@@ -165,6 +176,7 @@ __device__ __forceinline__ int drive(E& eng, uint64_t nr, Emit& emit,
 // stream's consumed position.
 
 struct NoEmit {
+    static constexpr bool kPairRounds = false;
     template <int K, class E> __device__ __forceinline__ void full(const E&) {}
     template <int K, class E> __device__ __forceinline__ void tail(const E&, uint64_t) {}
 };
@@ -173,6 +185,9 @@ template <class E, int OUT, bool VEC>
 struct Emit {
     static constexpr int W = E::WPL_;
     static constexpr int RW = E::RW;
+    // normals with one pair per lane per round and a two-row ring: the
+    // driver runs both rounds, then full_rounds01 (packed transform)
+    static constexpr bool kPairRounds = (OUT == kNormal || OUT == kNormalSum) && W == 2 && E::NROWS == 2;
     uint32_t* dst;     // this lane's first word of the current round
     uint64_t limit;    // outputs wanted (normals: n, words otherwise)
     uint64_t lane_off; // W * lane
@@ -214,6 +229,34 @@ struct Emit {
         dst += RW;
     }
 
+    // Rounds 0 and 1 of a two-row ring (kPairRounds): the outputs of
+    // full<0>() then full<1>(), both normal pairs through normal_pair2.
+    __device__ __forceinline__ void full_rounds01(const E& eng)
+    {
+        uint32_t oa[W], ob[W];
+        words<0>(eng, oa);
+        words<1>(eng, ob);
+        float z1a, z2a, z1b, z2b;
+        normal_pair2(oa[0], oa[1], ob[0], ob[1], z1a, z2a, z1b, z2b);
+        if constexpr (OUT != kNormalSum) {
+            if constexpr (VEC) {
+                *reinterpret_cast<uint2*>(dst) = make_uint2(__float_as_uint(z1a), __float_as_uint(z2a));
+                *reinterpret_cast<uint2*>(dst + RW) = make_uint2(__float_as_uint(z1b), __float_as_uint(z2b));
+            } else {
+                dst[0] = __float_as_uint(z1a);
+                dst[1] = __float_as_uint(z2a);
+                dst[RW] = __float_as_uint(z1b);
+                dst[RW + 1] = __float_as_uint(z2b);
+            }
+        } else {
+            acc = __fadd_rn(acc, z1a);
+            acc = __fadd_rn(acc, z2a);
+            acc = __fadd_rn(acc, z1b);
+            acc = __fadd_rn(acc, z2b);
+        }
+        dst += 2 * RW;
+    }
+
     template <int K>
     __device__ __forceinline__ void tail(const E& eng, uint64_t round)
     {
@@ -242,6 +285,17 @@ struct Emit {
         } else if constexpr (OUT == kUniform) {
 #pragma unroll
             for (int i = 0; i < W; ++i) v[i] = __float_as_uint(to_uniform(o[i]));
+        } else if constexpr (W % 4 == 0) {
+            // two pairs per lane per round: the packed transform
+#pragma unroll
+            for (int i = 0; i < W; i += 4) {
+                float z1a, z2a, z1b, z2b;
+                normal_pair2(o[i], o[i + 1], o[i + 2], o[i + 3], z1a, z2a, z1b, z2b);
+                v[i] = __float_as_uint(z1a);
+                v[i + 1] = __float_as_uint(z2a);
+                v[i + 2] = __float_as_uint(z1b);
+                v[i + 3] = __float_as_uint(z2b);
+            }
         } else {
             static_assert(W % 2 == 0, "normals pair words inside a lane");
 #pragma unroll

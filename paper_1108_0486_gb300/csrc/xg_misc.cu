@@ -30,16 +30,27 @@ __global__ void __launch_bounds__(256) transform_uniform_kernel(const uint32_t* 
         out[i] = to_uniform(in[i]);
 }
 
-// Box-Muller on pairs (in[2i], in[2i+1]) -> (out[2i], out[2i+1]).
+// Box-Muller on pairs (in[2i], in[2i+1]) -> (out[2i], out[2i+1]): two pairs
+// per thread through the packed transform the generation kernels use (the
+// same bits as normal_pair), the odd last pair alone.
 __global__ void __launch_bounds__(256) transform_normal_kernel(const uint32_t* __restrict__ in,
                                                                 uint64_t npairs, float* __restrict__ out)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride) {
-        const uint2 w = reinterpret_cast<const uint2*>(in)[i];
+    const uint64_t nquads = npairs / 2;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nquads; i += stride) {
+        const uint2 a = reinterpret_cast<const uint2*>(in)[2 * i];
+        const uint2 b = reinterpret_cast<const uint2*>(in)[2 * i + 1];
+        float z1a, z2a, z1b, z2b;
+        normal_pair2(a.x, a.y, b.x, b.y, z1a, z2a, z1b, z2b);
+        reinterpret_cast<float2*>(out)[2 * i] = make_float2(z1a, z2a);
+        reinterpret_cast<float2*>(out)[2 * i + 1] = make_float2(z1b, z2b);
+    }
+    if ((npairs & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint2 w = reinterpret_cast<const uint2*>(in)[npairs - 1];
         float z1, z2;
         normal_pair(w.x, w.y, z1, z2);
-        reinterpret_cast<float2*>(out)[i] = make_float2(z1, z2);
+        reinterpret_cast<float2*>(out)[npairs - 1] = make_float2(z1, z2);
     }
 }
 

@@ -258,6 +258,40 @@ def test_normal_angle_all_m2():
     assert np.all(z[ref == 0.0] == 0.0)
 
 
+def test_normal_bits_same_at_every_launch():
+    """The (32,2) launch runs the normal transform two pairs at a time with
+    packed FP32x2 instructions; the other launches one pair at a time.  Every
+    launch gives the same bits (ragged lengths, odd counts, both sets); the
+    fused sums are checked per launch by test_fused_normal_sum."""
+    for ps in (0, 1):
+        seeds = W.seeds(50, start=311)
+        outs = []
+        for tpg, wpl in LAUNCHES:
+            with Streams(50, param_set=ps, seeds=seeds) as st:
+                st.set_launch("normal", tpg, wpl)
+                z = [st.normal(n).cpu().numpy() for n in (1, 257, 4096 + 3, 20000)]
+            outs.append(z)
+        ref_z = outs[-1]
+        for z, (tpg, wpl) in zip(outs, LAUNCHES):
+            for a, b in zip(z, ref_z):
+                assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), (ps, tpg, wpl)
+
+
+def test_normal_transform_packed_and_scalar_agree():
+    """The stand-alone transform (two pairs per thread, packed) on an odd
+    number of pairs (the last one alone) against the oracle, and against
+    the same words run as one pair per call."""
+    rng = np.random.default_rng(21)
+    words = rng.integers(0, 2**32, 2 * 100001, dtype=np.uint64).astype(np.uint32)
+    words[:64] = (np.arange(64, dtype=np.uint32) << 8)   # the FP64 tail in some quads
+    z = _transform(words)
+    err = ulp_error(z, O.normal_pairs64(words))
+    assert float(err.max()) <= NORMAL_TOL_ULP, err.max()
+    single = np.concatenate([_transform(words[2 * i:2 * i + 2]) for i in (0, 1, 2, 63, 64, 99999, 100000)])
+    assert np.array_equal(single.view(np.uint32),
+                          np.concatenate([z[2 * i:2 * i + 2] for i in (0, 1, 2, 63, 64, 99999, 100000)]).view(np.uint32))
+
+
 def test_normal_random_pairs():
     rng = np.random.default_rng(11)
     words = rng.integers(0, 2**32, 1 << 25, dtype=np.uint64).astype(np.uint32)
