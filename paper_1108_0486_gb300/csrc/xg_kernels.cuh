@@ -148,11 +148,17 @@ __device__ __forceinline__ int drive(E& eng, uint64_t nr, Emit& emit,
         }
     }
     while (r + E::NROWS < nr) {
-        static_for<0, E::NROWS>([&](auto kc) {
-            constexpr int K = decltype(kc)::value;
-            eng.template round<K>();
-            emit.template full<K>(eng);
-        });
+        if constexpr (Emit::kPairRounds) {
+            eng.template round<0>();
+            eng.template round<1>();
+            emit.full_rounds01(eng);
+        } else {
+            static_for<0, E::NROWS>([&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+                eng.template round<K>();
+                emit.template full<K>(eng);
+            });
+        }
         r += E::NROWS;
     }
     const int rem = (int)(nr - r);
