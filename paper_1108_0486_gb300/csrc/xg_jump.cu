@@ -538,50 +538,42 @@ extern "C" xg_status xg_seed_substreams(xg_ctx* ctx, uint32_t first, uint32_t co
     xg_status st = XG_OK;
     for (int b = 0; b < steps; ++b)
         if (!jump_matrix(ctx->device, (int)ctx->param_set, q + b, s, &st)) return st;
-    // host lists: [first] | per step b, sources m - 2^b then destinations m,
-    // for m in [2^b, min(2^(b+1), count))
-    std::vector<uint32_t> h(1 + 2 * (size_t)(count - 1));
-    h[0] = first;
-    std::vector<size_t> src_off(steps), dst_off(steps);
-    std::vector<uint32_t> cnt(steps);
-    size_t o = 1;
+    // step b takes the states m - 2^b to the states m, m in [2^b, min(2^(b+1), count)):
+    // its sources are the identity list from 0 and its destinations the same
+    // list from 2^b, so one device-built list 0 .. 2 count - 1 serves every step
+    uint32_t most = 0;
     for (int b = 0; b < steps; ++b) {
         const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, count);
-        cnt[b] = hi - lo;
-        src_off[b] = o;
-        for (uint32_t m = lo; m < hi; ++m) h[o++] = m - lo;
-        dst_off[b] = o;
-        for (uint32_t m = lo; m < hi; ++m) h[o++] = m;
+        most = std::max(most, hi - lo);
     }
-    uint32_t* rings = nullptr;
-    uint32_t* lists = nullptr;   // the host lists, then the gathered Weyl word
-    uint8_t* scratch = nullptr;  // tensor-core operand (when used)
-    const uint32_t most = steps ? *std::max_element(cnt.begin(), cnt.end()) : 0u;
+    // workspace kept in the context (grow-only): rings of all count states;
+    // the index lists (first + i, then 0 .. 2 count - 1); the gathered Weyl
+    // word; the tensor-core operand (when used)
+    const size_t rings_bytes = (size_t)count * kR * 4;
+    const size_t ids_off = rings_bytes;
+    const size_t w0_off = ids_off + (size_t)3 * count * 4;
+    const size_t scratch_off = (w0_off + 4 + 255) / 256 * 256;
     const size_t sbytes = gf2_apply_scratch(ctx->device, most);
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)count * kR * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&lists), (h.size() + 1) * 4, s);
-    if (e == cudaSuccess && sbytes) e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sbytes, s);
-    if (e != cudaSuccess) {
-        if (rings) cudaFreeAsync(rings, s);
-        if (lists) cudaFreeAsync(lists, s);
-        return cuda_fail(e, "xg_seed_substreams scratch");
+    if (xg_status g = ctx->ensure_jump_ws(scratch_off + sbytes)) return g;
+    char* ws = static_cast<char*>(ctx->jump_ws);
+    uint32_t* rings = reinterpret_cast<uint32_t*>(ws);
+    uint32_t* ids = reinterpret_cast<uint32_t*>(ws + ids_off);
+    const uint32_t* iota = ids + count;
+    uint32_t* d_w0 = reinterpret_cast<uint32_t*>(ws + w0_off);
+    uint8_t* scratch = sbytes ? reinterpret_cast<uint8_t*>(ws + scratch_off) : nullptr;
+    cudaError_t e = launch_jump_index(ids, count, first, s);
+    if (e == cudaSuccess) e = launch_gather_rings(ctx->st, ids, 1, rings, nullptr, d_w0, 1, 0u, s);
+    for (int b = 0; b < steps && e == cudaSuccess; ++b) {
+        const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, count);
+        e = gf2_apply(ctx->device, (int)ctx->param_set, q + b, rings, hi - lo, iota, iota + lo, scratch,
+                      ctx->sm_count, s, &st);
     }
-    uint32_t* d_w0 = lists + h.size();
-    e = cudaMemcpyAsync(lists, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = launch_gather_rings(ctx->st, lists, 1, rings, nullptr, d_w0, 1, 0u, s);
-    for (int b = 0; b < steps && e == cudaSuccess; ++b)
-        e = gf2_apply(ctx->device, (int)ctx->param_set, q + b, rings, cnt[b], lists + src_off[b], lists + dst_off[b],
-                      scratch, ctx->sm_count, s, &st);
     if (e == cudaSuccess) {
         substream_scatter_kernel<<<count, 128, 0, s>>>(ctx->st, first, count, rings, d_w0, q,
                                                        ctx->weyl_on ? 0x9E3779B9u : 0u);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
-    cudaFreeAsync(rings, s);
-    cudaFreeAsync(lists, s);
-    if (scratch) cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (st != XG_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "xg_seed_substreams");
     if (sbytes && gf2_tc_take_failure())

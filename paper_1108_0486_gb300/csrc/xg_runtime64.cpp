@@ -449,47 +449,43 @@ xg_status xg_w64_seed_substreams(xg_w64_ctx* c, uint32_t first, uint32_t count, 
     xg_status st = XG_OK;
     for (int b = 0; b < steps; ++b)
         if (!xg::jump_matrix(c->device, xg::kJumpSetW64, q + b, s, &st)) return st;
-    // per step b: sources m - 2^b, then destinations m, m in [2^b, min(2^(b+1), count))
-    std::vector<uint32_t> h(2 * (size_t)(count - 1) + 1);
-    std::vector<size_t> src_off(steps), dst_off(steps);
-    std::vector<uint32_t> cnt(steps);
-    size_t o = 0;
+    // step b takes the states m - 2^b to the states m, m in [2^b, min(2^(b+1), count)):
+    // its sources are the identity list from 0 and its destinations the same
+    // list from 2^b, so one device-built list 0 .. 2 count - 1 serves every step
+    uint32_t most = 0;
     for (int b = 0; b < steps; ++b) {
         const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, count);
-        cnt[b] = hi - lo;
-        src_off[b] = o;
-        for (uint32_t m = lo; m < hi; ++m) h[o++] = m - lo;
-        dst_off[b] = o;
-        for (uint32_t m = lo; m < hi; ++m) h[o++] = m;
+        most = std::max(most, hi - lo);
     }
-    uint64_t* rings = nullptr;
-    uint32_t* lists = nullptr;   // the pair lists, then (8-byte aligned) the base Weyl word
-    uint8_t* tc_scratch = nullptr;  // tensor-core operand, when used
-    const uint32_t most = steps ? *std::max_element(cnt.begin(), cnt.end()) : 0u;
+    // one workspace: rings of all count states; the index lists (0 .. count - 1,
+    // then 0 .. 2 count - 1); the base Weyl word (8-byte aligned); the
+    // tensor-core operand (256-byte aligned, when used)
+    const size_t rings_bytes = (size_t)count * xg64::kR * 8;
+    const size_t ids_off = rings_bytes;
+    const size_t w0_off = (ids_off + (size_t)3 * count * 4 + 7) / 8 * 8;
+    const size_t tc_off = (w0_off + 8 + 255) / 256 * 256;
     const size_t tc_bytes = xg::gf2_apply_scratch(c->device, most);
-    const size_t w0_off = (h.size() * 4 + 7) / 8 * 8;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rings), (size_t)count * xg64::kR * 8, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&lists), w0_off + 8, s);
-    if (e == cudaSuccess && tc_bytes) e = cudaMallocAsync(reinterpret_cast<void**>(&tc_scratch), tc_bytes, s);
-    if (e != cudaSuccess) {
-        if (rings) cudaFreeAsync(rings, s);
-        if (lists) cudaFreeAsync(lists, s);
-        return cuda_fail(e, "xg_w64_seed_substreams scratch");
-    }
-    uint64_t* d_w0 = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(lists) + w0_off);
+    char* ws = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), tc_off + tc_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "xg_w64_seed_substreams scratch");
+    uint64_t* rings = reinterpret_cast<uint64_t*>(ws);
+    uint32_t* ids = reinterpret_cast<uint32_t*>(ws + ids_off);
+    const uint32_t* iota = ids + count;
+    uint64_t* d_w0 = reinterpret_cast<uint64_t*>(ws + w0_off);
+    uint8_t* tc_scratch = tc_bytes ? reinterpret_cast<uint8_t*>(ws + tc_off) : nullptr;
     uint32_t* rings32 = reinterpret_cast<uint32_t*>(rings);
-    e = cudaMemcpyAsync(lists, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
+    e = xg::launch_jump_index(ids, count, 0u, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_w0, c->st.weyl + first, 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = xg64::launch_gather_rings(c->st, first, 1, rings, s);
-    for (int b = 0; b < steps && e == cudaSuccess; ++b)
-        e = xg::gf2_apply(c->device, xg::kJumpSetW64, q + b, rings32, cnt[b], lists + src_off[b], lists + dst_off[b],
-                          tc_scratch, c->sm_count, s, &st);
+    for (int b = 0; b < steps && e == cudaSuccess; ++b) {
+        const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, count);
+        e = xg::gf2_apply(c->device, xg::kJumpSetW64, q + b, rings32, hi - lo, iota, iota + lo, tc_scratch,
+                          c->sm_count, s, &st);
+    }
     if (e == cudaSuccess)
         e = xg64::launch_substream_scatter(c->st, first, count, rings, d_w0, q, c->weyl_on ? xg64::kOmega : 0, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h is a host temporary
-    cudaFreeAsync(rings, s);
-    cudaFreeAsync(lists, s);
-    if (tc_scratch) cudaFreeAsync(tc_scratch, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(ws, s);
     if (st != XG_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "xg_w64_seed_substreams");
     if (tc_bytes && xg::gf2_tc_take_failure())
