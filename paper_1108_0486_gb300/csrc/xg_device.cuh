@@ -39,10 +39,17 @@ using ParamsDefault = Params<95, 17, 12, 13, 15>;
 // (r,s,a,b,c,d) = (128,65,15,14,12,17): the set of the paper's results (Sec. 2).
 using ParamsPaper = Params<65, 15, 14, 12, 17>;
 
-// Eq. (1): w (I + R^gamma) + x mod 2^32.
+// The integer 1 as a value the compiler cannot fold: the grid's depth (every
+// kernel here that runs the recurrence is launched on a grid of depth 1).
+// x * grid_unit() + y and x * (grid_unit() << k) then issue as integer
+// multiply-adds on the FMA pipe rather than as adds and shifts on the ALU
+// pipe, which the recurrence and the normal transform keep the busiest.
+__device__ __forceinline__ uint32_t grid_unit() { return gridDim.z; }
+
+// Eq. (1): w (I + R^gamma) + x mod 2^32 (the sum as a multiply-add).
 __device__ __forceinline__ uint32_t combine(uint32_t x, uint32_t w)
 {
-    return x + (w ^ (w >> kGamma));
+    return (w ^ (w >> kGamma)) * grid_unit() + x;
 }
 
 // Uniform in [0,1): (out >> 8) * 2^-24; exact in binary32.
@@ -90,11 +97,13 @@ __device__ __forceinline__ float neg2ln_u1(uint32_t m1)
 // sqrt(L) with one Newton correction of the hardware reciprocal square root
 // (rsqrt.approx with denormals flushed: L is 0 or at least 1.19e-7, and the
 // guard keeps 0 away, so no input is subnormal and the flush changes no result;
-// it spares the subnormal handling around the approximation).
+// it spares the subnormal handling around the approximation).  The guard is
+// L + 2^-100 (an FMA-pipe addition): it gives 2^-100 for L = 0 and L itself
+// for every other L, whose half ulp is far above 2^-100.
 __device__ __forceinline__ float sqrt_refined(float L)
 {
     float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaxf(L, 0x1p-100f)));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__fadd_rn(L, 0x1p-100f)));
     const float r0 = __fmul_rn(L, y);
     const float d = __fmaf_rn(-r0, r0, L);
     return __fmaf_rn(d, __fmul_rn(0.5f, y), r0);
@@ -221,10 +230,11 @@ __device__ __forceinline__ void normal_pair2(uint32_t o1a, uint32_t o2a, uint32_
     const f32x2 lnf = fma2(mul2(t, t), q, t);
     const f32x2 e = pk2(__int2float_rn(da >> 23), __int2float_rn(db >> 23));
     const f32x2 L = fma2(e, dup2(kNeg2Ln2Hi), fma2(e, dup2(kNeg2Ln2Lo), mul2(dup2(-2.0f), lnf)));
-    // R = sqrt(L): sqrt_refined on both halves
+    // R = sqrt(L): sqrt_refined on both halves (its guard as one packed addition)
+    const f32x2 Lg = add2(L, dup2(0x1p-100f));
     float ya, yb;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ya) : "f"(fmaxf(lo2(L), 0x1p-100f)));
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yb) : "f"(fmaxf(hi2(L), 0x1p-100f)));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ya) : "f"(lo2(Lg)));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yb) : "f"(hi2(Lg)));
     const f32x2 y = pk2(ya, yb);
     const f32x2 r0 = mul2(L, y);
     const f32x2 dd = fma2(mul2(r0, dup2(-1.0f)), r0, L);         // -r0 exact
@@ -304,10 +314,10 @@ struct Engine {
 #pragma unroll
         for (int i = 0; i < WPL; ++i) {
             uint32_t t = ring[K][i];
-            t ^= t << P::A;
+            t ^= t * (grid_unit() << P::A);   // t << a, as a multiplication
             t ^= t >> P::B;
             uint32_t u = v[i];
-            u ^= u << P::C;
+            u ^= u * (grid_unit() << P::C);   // u << c
             u ^= u >> P::D;
             ring[K][i] = t ^ u;
         }
