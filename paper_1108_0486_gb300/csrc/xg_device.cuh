@@ -170,6 +170,16 @@ __device__ __forceinline__ void normal_pair(uint32_t o1, uint32_t o2, float& z1,
 // the same bits as two calls of normal_pair; the integer steps, the
 // conversions, the reciprocal square root and the quadrant selection stay
 // scalar.  If either pair takes the FP64 tail, both go through normal_pair.
+// Three rewrites of normal_pair's steps that keep every bit and take work off
+// the ALU pipe (tested against normal_pair at every launch shape):
+//  * the exponent split starts from u1 = m1 2^-24 (an exact packed product):
+//    k = (bits(u1) - bits(sqrt(1/2))) >> 23 and bits(f) = bits(u1) - k 2^23,
+//    one integer multiply-add instead of a mask and an addition;
+//  * the radius is carried negated (-L, -r0, -R; round-to-nearest is
+//    symmetric, so each is the exact negative of normal_pair's value) and the
+//    sign flips absorb the extra sign;
+//  * the sign flips read o2 directly: bit 31 of o2 + 3 2^29 (cosine) and of
+//    o2 + 2^29 (sine) are bit 23 of mm + 2^22 and of mm.
 using f32x2 = unsigned long long;
 
 __device__ __forceinline__ f32x2 pk2(float lo, float hi)
@@ -220,25 +230,29 @@ __device__ __forceinline__ void normal_pair2(uint32_t o1a, uint32_t o2a, uint32_
         return;
     }
     // radius: the exponent split of neg2ln_u1, per pair
-    const int da = __float_as_int(__uint2float_rn(m1a)) - (0x3F3504F3 + (24 << 23));
-    const int db = __float_as_int(__uint2float_rn(m1b)) - (0x3F3504F3 + (24 << 23));
-    const f32x2 f = pk2(__int_as_float((da & 0x7FFFFF) + 0x3F3504F3), __int_as_float((db & 0x7FFFFF) + 0x3F3504F3));
+    const f32x2 u1 = mul2(pk2(__uint2float_rn(m1a), __uint2float_rn(m1b)), dup2(0x1p-24f));   // exact
+    const int ba = __float_as_int(lo2(u1)), bb = __float_as_int(hi2(u1));
+    const int ka = (ba - 0x3F3504F3) >> 23, kb = (bb - 0x3F3504F3) >> 23;   // u1 = 2^k f
+    const uint32_t m23 = 0u - (grid_unit() << 23);                           // -2^23
+    const f32x2 f = pk2(__int_as_float((int)((uint32_t)ka * m23 + (uint32_t)ba)),
+                        __int_as_float((int)((uint32_t)kb * m23 + (uint32_t)bb)));
     const f32x2 t = add2(f, dup2(-1.0f));                          // exact
     f32x2 q = dup2(kLogQ[8]);
 #pragma unroll
     for (int i = 7; i >= 0; --i) q = fma2(q, t, dup2(kLogQ[i]));
     const f32x2 lnf = fma2(mul2(t, t), q, t);
-    const f32x2 e = pk2(__int2float_rn(da >> 23), __int2float_rn(db >> 23));
-    const f32x2 L = fma2(e, dup2(kNeg2Ln2Hi), fma2(e, dup2(kNeg2Ln2Lo), mul2(dup2(-2.0f), lnf)));
-    // R = sqrt(L): sqrt_refined on both halves (its guard as one packed addition)
-    const f32x2 Lg = add2(L, dup2(0x1p-100f));
+    const f32x2 e = pk2(__int2float_rn(ka), __int2float_rn(kb));
+    const f32x2 nL = fma2(e, dup2(-kNeg2Ln2Hi), fma2(e, dup2(-kNeg2Ln2Lo), mul2(dup2(2.0f), lnf)));   // -L
+    // R = sqrt(L): sqrt_refined on both halves (its guard as one packed
+    // addition), carried as -r0, -d and -R
+    const f32x2 nLg = add2(nL, dup2(-0x1p-100f));
     float ya, yb;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ya) : "f"(lo2(Lg)));
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yb) : "f"(hi2(Lg)));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ya) : "f"(-lo2(nLg)));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yb) : "f"(-hi2(nLg)));
     const f32x2 y = pk2(ya, yb);
-    const f32x2 r0 = mul2(L, y);
-    const f32x2 dd = fma2(mul2(r0, dup2(-1.0f)), r0, L);         // -r0 exact
-    const f32x2 R = fma2(dd, mul2(dup2(0.5f), y), r0);
+    const f32x2 nr0 = mul2(nL, y);
+    const f32x2 nd = fma2(nr0, nr0, nL);
+    const f32x2 nR = fma2(nd, mul2(dup2(0.5f), y), nr0);
     // angle: normal_pair's exact reduction, per pair for the integer parts
     const uint32_t mma = (o2a >> 8) + (1u << 21), mmb = (o2b >> 8) + (1u << 21);
     const f32x2 xq = add2(pk2(__uint_as_float((mma & 0x3FFFFFu) | 0x3F800000u),
@@ -259,10 +273,13 @@ __device__ __forceinline__ void normal_pair2(uint32_t o1a, uint32_t o2a, uint32_
     const bool odda = (mma >> 22) & 1u, oddb = (mmb >> 22) & 1u;
     const float csa = odda ? sa : ca, sna = odda ? ca : sa;
     const float csb = oddb ? sb : cb, snb = oddb ? cb : sb;
-    const uint32_t cfa = ((mma + (1u << 22)) << 8) & 0x80000000u, sfa = (mma << 8) & 0x80000000u;
-    const uint32_t cfb = ((mmb + (1u << 22)) << 8) & 0x80000000u, sfb = (mmb << 8) & 0x80000000u;
-    const f32x2 z1 = mul2(R, pk2(__uint_as_float(__float_as_uint(csa) ^ cfa), __uint_as_float(__float_as_uint(csb) ^ cfb)));
-    const f32x2 z2 = mul2(R, pk2(__uint_as_float(__float_as_uint(sna) ^ sfa), __uint_as_float(__float_as_uint(snb) ^ sfb)));
+    // the flips of normal_pair, inverted for the negated radius
+    const uint32_t cfa = ~(o2a * grid_unit() + 0x60000000u) & 0x80000000u;
+    const uint32_t sfa = ~(o2a * grid_unit() + 0x20000000u) & 0x80000000u;
+    const uint32_t cfb = ~(o2b * grid_unit() + 0x60000000u) & 0x80000000u;
+    const uint32_t sfb = ~(o2b * grid_unit() + 0x20000000u) & 0x80000000u;
+    const f32x2 z1 = mul2(nR, pk2(__uint_as_float(__float_as_uint(csa) ^ cfa), __uint_as_float(__float_as_uint(csb) ^ cfb)));
+    const f32x2 z2 = mul2(nR, pk2(__uint_as_float(__float_as_uint(sna) ^ sfa), __uint_as_float(__float_as_uint(snb) ^ sfb)));
     z1a = lo2(z1);
     z1b = hi2(z1);
     z2a = lo2(z2);
