@@ -458,7 +458,7 @@ def run_ours(args):
     bytes_per_launch = STREAMS * N_PER * 4
     avg_u = sum(ms_u) / len(ms_u)
     avg_f = sum(ms_f) / len(ms_f)
-    dom_ms, dom_name = (avg_u, "gen_kernel<u32>") if avg_u >= avg_f else (avg_f, "gen_kernel<uniform>")
+    dom_ms, dom_name = (avg_u, "gen_kernel<u32>") if avg_u >= avg_f else (avg_f, "gen_kernel_ilp<uniform>")
     achieved = bytes_per_launch / (dom_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
