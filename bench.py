@@ -484,6 +484,7 @@ def run_ours(args):
         rows["batched"] = batched_row(torch, L, stream, peak)
         rows["serving"] = serving_row(torch, L, stream, seconds=args.serve_seconds)
         rows["serving_sweep"] = serving_sweep(torch, L, stream)
+        rows["serving_sweep_u32_uniform"] = serving_sweep_words(torch, L, stream, peak)
         try:
             rows["curand_xorwow_context"] = curand_row(torch, stream)
         except Exception as e:  # context only: never fail the bench on it
@@ -840,17 +841,19 @@ def serving_row(torch, L, stream, seconds=10.0, plain_seconds=2.0, rate=20000.0,
     return row
 
 
-def serving_bulk(torch, L, stream, rate, seconds, lanes=48, max_batch=1024, split=0, cap_gib=16, size_scale=1):
-    """Open-loop Poisson arrivals at `rate`, the serving row's mix, submitted
-    by one host thread in bulk (xg_submit_many: every request that has
-    arrived by the time of the call), library pool outputs released by a
-    reaper that drains completions in bulk.  Latency = completion minus
-    arrival, both on CLOCK_MONOTONIC (the server's clock)."""
+def serving_bulk(torch, L, stream, rate, seconds, lanes=48, max_batch=1024, split=0, cap_gib=16, size_scale=1,
+                 mix=(0.1, 0.3, 0.6)):
+    """Open-loop Poisson arrivals at `rate`, the serving row's mix (or `mix`
+    = (u32, uniform, normal) weights), submitted by one host thread in bulk
+    (xg_submit_many: every request that has arrived by the time of the
+    call), library pool outputs released by a reaper that drains completions
+    in bulk.  Latency = completion minus arrival, both on CLOCK_MONOTONIC
+    (the server's clock)."""
     import threading as th
     from paper_1108_0486_gb300 import Streams
     S = 65536
     reqs = W.serving_requests(n_streams=S, rate=rate, duration=seconds, lo=(1 << 10) * size_scale,
-                              hi=(1 << 22) * size_scale)
+                              hi=(1 << 22) * size_scale, mix=mix)
     n = len(reqs)
     rec = L.make_requests([(r.stream, r.kind, r.count, 0) for r in reqs])
     arrival = np.array([r.t_arrival for r in reqs])
@@ -932,6 +935,20 @@ def serving_sweep(torch, L, stream, rates=(40000.0, 160000.0, 640000.0, 1280000.
     latency (from arrival) and delivered RN/s as the Poisson rate grows past
     what the GPU can serve."""
     return [serving_bulk(torch, L, stream, rate, seconds) for rate in rates]
+
+
+def serving_sweep_words(torch, L, stream, peak, rates=(320000.0, 640000.0, 1280000.0), seconds=0.25):
+    """The served path without normals: the same server and bulk submission,
+    requests half u32 and half uniforms of 2^12..2^24 words (log-uniform), as
+    the rate passes the HBM write bound; hbm_frac = delivered bytes / the
+    measured copy rate."""
+    out = []
+    for rate in rates:
+        r = serving_bulk(torch, L, stream, rate, seconds, size_scale=4, mix=(0.5, 0.5, 0.0))
+        r["hbm_frac"] = r["delivered_rn_s"] * 4 / (peak * 1e9)
+        out.append(r)
+    return {"workload": "65536 streams, Poisson arrivals, sizes log-uniform [2^12, 2^24], 50/50 u32/uniform "
+                        "(PCG64 seed 486), cap 16 GiB, bulk submission, 0.25 s windows", "points": out}
 
 
 def curand_row(torch, stream, n=1 << 30):
