@@ -437,8 +437,10 @@ static cudaError_t launch_pairs(const uint64_t* C, uint32_t* rings, uint32_t n, 
 {
     const uint32_t groups = (n + NV - 1) / NV;
     // enough blocks for about 8 per SM, splitting the 4096 columns if needed
+    // (down to one 32-column input word per block: with few states the
+    // matrix read is the cost, spread over up to 128 blocks)
     int chunks = 1;
-    while (chunks < 32 && (uint64_t)groups * chunks < (uint64_t)8 * sm_count) chunks *= 2;
+    while (chunks < kBits / 32 && (uint64_t)groups * chunks < (uint64_t)8 * sm_count) chunks *= 2;
     gf2_apply_pairs_kernel<NV><<<dim3(groups, chunks), 128, 0, s>>>(reinterpret_cast<const uint32_t*>(C), rings,
                                                                    d_src, d_dst, n, rings, kBits / chunks);
     return cudaGetLastError();
