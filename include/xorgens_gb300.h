@@ -54,7 +54,10 @@ typedef enum {
     XG_ECUDA = 5,      /* a CUDA runtime call failed (message has the CUDA error) */
     XG_ENOTFOUND = 6,  /* unknown ticket */
     XG_EDEVICE = 7,    /* device-side state read back by the host is corrupt (xg_get_state),
-                          or a server request's batch failed to launch and never ran */
+                          a server request's batch failed to launch and never ran, or a
+                          jump-ahead kernel on the tensor cores gave up one of its bounded
+                          waits (xg_jump, xg_seed_substreams, a cut call: the streams being
+                          advanced are not valid; reseed or restore them) */
     XG_ECANCELED = 8   /* the request was cancelled (xg_cancel) before it ran */
 } xg_status;
 

@@ -24,11 +24,15 @@
 //
 // Every wait is bounded (2 s of %globaltimer); a wait that gives up records
 // a failure in a host-visible status word, the CTA waits (bounded) for its
-// own TMA copies still in flight, frees its TMEM and returns.
+// own TMA copies still in flight, frees its TMEM and returns.  To test that
+// path, XG_TC_TEST_STALL=1 in the environment makes CTA 0 arm its first
+// stage's barrier without starting the stage's copies: the waits on that
+// stage run out (no fault, no unbounded wait) and the call reports it.
 #include <cuda.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 
 #include "xg_gf2_tc.h"
@@ -171,7 +175,7 @@ __device__ __forceinline__ bool failed(const volatile int* flag) { return *flag 
 __global__ void __launch_bounds__(kThreads, 1) gf2_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB, uint32_t n,
                                                               uint32_t n_tiles, const uint32_t* __restrict__ dst,
-                                                              uint32_t* rings, uint32_t* status)
+                                                              uint32_t* rings, uint32_t* status, uint32_t stall)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) gf2_tc_kernel(const __grid_consta
                         break;
                     }
                     mbar_expect_tx(&full[s], kStageBytes);
+                    if (stall && blockIdx.x == 0 && issued == 0) continue;   // the failure-path test
                     tma_load_2d(sa + s * kABytes, &tmA, &full[s], kb * kBK, mt * kBM);
                     tma_load_2d(sb + s * kBBytes, &tmB, &full[s], kb * kBK, nt * kBN);
                 }
@@ -458,7 +463,9 @@ cudaError_t gf2_tc_apply(int device, const uint8_t* A, const uint32_t* rings_in,
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 1;
     const unsigned grid = (unsigned)std::min<uint32_t>(tiles, (uint32_t)sms);
-    gf2_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(ma, mb, n, n_tiles, dst, rings_out, g_status_dev);
+    const char* stall = std::getenv("XG_TC_TEST_STALL");
+    gf2_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(ma, mb, n, n_tiles, dst, rings_out, g_status_dev,
+                                                     (stall && stall[0] == '1') ? 1u : 0u);
     return cudaGetLastError();
 }
 

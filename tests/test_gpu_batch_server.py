@@ -859,3 +859,28 @@ def test_server_cancel_queued_requests():
     for i in kept:
         assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), seq[off:off + sizes[i]]), i
         off += sizes[i]
+
+
+def test_tensor_core_wait_that_runs_out_reports_a_device_error(monkeypatch):
+    """The failure path of the tensor-core kernel's bounded waits.  With
+    XG_TC_TEST_STALL=1 its first CTA arms the first stage's barrier but starts
+    none of that stage's copies, so the waits on the stage give up after 2 s;
+    the kernel then waits (bounded) for its copies in flight, frees its TMEM
+    and returns.  The jump reports XG_EDEVICE, and the context and the GPU
+    keep working: the same context, reseeded, jumps to the oracle's words."""
+    from paper_1108_0486_gb300 import _lib as L
+    monkeypatch.setenv("XG_GF2_TC_MIN_STATES", "1")
+    monkeypatch.setenv("XG_JUMP_TENSOR_CORES", "1")
+    seeds = W.seeds(4, start=9100)
+    J = (1 << 40) + 3
+    with Streams(4, seeds=seeds) as st:
+        monkeypatch.setenv("XG_TC_TEST_STALL", "1")
+        with pytest.raises(L.XGError) as err:
+            st.jump(1 << 20)
+        assert err.value.status == L.XG_EDEVICE and "gave up waiting" in str(err.value)
+        monkeypatch.delenv("XG_TC_TEST_STALL")
+        st.seed(seeds)
+        st.jump(J)
+        got = st.u32(32).cpu().numpy().view(np.uint32)
+    for i in range(4):
+        assert np.array_equal(got[i], O.u32_after_jump(int(seeds[i]), J, 32)), i
