@@ -394,7 +394,8 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
     if (cudaMemcpyAsync(db + off_streams, hb + off_streams, o - off_streams, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return XG_ECUDA;
-    // all rings gathered (the doubling steps overwrite the m > 0 ones: zero them first)
+    // piece 0 of each call gets its stream's ring, the others (nonzero skip)
+    // a zero ring, into which their doubling step XORs
     if (launch_gather_rings(c->st, reinterpret_cast<const uint32_t*>(db + off_streams), P,
                             reinterpret_cast<uint32_t*>(db + off_rings),
                             reinterpret_cast<const uint64_t*>(db + off_skip),
@@ -408,7 +409,7 @@ xg_status BatchLauncher::prologue(xg_ctx* c, cudaStream_t s)
         if (gf2_apply(c->device, (int)c->param_set, plan_.split_log2 + b, reinterpret_cast<uint32_t*>(db + off_rings),
                       per_step[b], reinterpret_cast<const uint32_t*>(db + src_off[b]),
                       reinterpret_cast<const uint32_t*>(db + dst_off[b]), tc_scratch, c->sm_count, s,
-                      &st) != cudaSuccess)
+                      &st, true) != cudaSuccess)
             return st != XG_OK ? st : XG_ECUDA;
     }
     return XG_OK;

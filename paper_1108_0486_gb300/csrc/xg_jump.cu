@@ -159,7 +159,9 @@ __global__ void zero_listed_kernel(uint32_t* __restrict__ rings, const uint32_t*
 }
 
 // Copy each listed stream's current ring (window at its pend offset) into
-// rings[k]; also rings' Weyl words advanced by skip[k] words.
+// rings[k]; also rings' Weyl words advanced by skip[k] words.  With skips,
+// an entry with a nonzero skip gets a zero ring instead: its ring is the
+// result of a later jump-ahead step, which XORs into it.
 __global__ void gather_rings_kernel(State st, const uint32_t* __restrict__ streams, uint32_t n,
                                     uint32_t* __restrict__ rings, const uint64_t* __restrict__ skip,
                                     uint32_t* __restrict__ weyl0, uint32_t weyl0_stride, uint32_t omega)
@@ -169,7 +171,8 @@ __global__ void gather_rings_kernel(State st, const uint32_t* __restrict__ strea
     const uint32_t s = streams[k];
     const uint32_t pend = st.pend[s];
     const uint32_t* src = st.win + (size_t)s * kWin + (kRingBase - pend);
-    for (int w = threadIdx.x; w < kR; w += blockDim.x) rings[(size_t)k * kR + w] = src[w];
+    const bool zero = skip && skip[k] != 0;
+    for (int w = threadIdx.x; w < kR; w += blockDim.x) rings[(size_t)k * kR + w] = zero ? 0u : src[w];
     if (threadIdx.x == 0 && weyl0)
         weyl0[(size_t)k * weyl0_stride] = st.weyl[s] + (uint32_t)(skip ? skip[k] : 0) * omega;
 }
@@ -314,7 +317,8 @@ size_t gf2_apply_scratch(int device, uint32_t n)
 }
 
 cudaError_t gf2_apply(int device, int family, int k, uint32_t* rings, uint32_t n, const uint32_t* d_src,
-                      const uint32_t* d_dst, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st)
+                      const uint32_t* d_dst, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st,
+                      bool dst_zeroed)
 {
     *st = XG_OK;
     if (n == 0) return cudaSuccess;
@@ -325,7 +329,7 @@ cudaError_t gf2_apply(int device, int family, int k, uint32_t* rings, uint32_t n
     }
     const uint64_t* C = jump_matrix(device, family, k, s, st);
     if (!C) return cudaErrorMemoryAllocation;
-    cudaError_t e = zero_rings(rings, d_dst, n, s);
+    cudaError_t e = dst_zeroed ? cudaSuccess : zero_rings(rings, d_dst, n, s);
     if (e == cudaSuccess) e = launch_gf2_apply_pairs(C, rings, n, d_src, d_dst, sm_count, s);
     return e;
 }
@@ -565,10 +569,12 @@ extern "C" xg_status xg_seed_substreams(xg_ctx* ctx, uint32_t first, uint32_t co
     uint8_t* scratch = sbytes ? reinterpret_cast<uint8_t*>(ws + scratch_off) : nullptr;
     cudaError_t e = launch_jump_index(ids, count, first, s);
     if (e == cudaSuccess) e = launch_gather_rings(ctx->st, ids, 1, rings, nullptr, d_w0, 1, 0u, s);
+    // the destinations 1 .. count - 1, zeroed once for all the steps
+    if (e == cudaSuccess && count > 1) e = cudaMemsetAsync(rings + kR, 0, (size_t)(count - 1) * kR * 4, s);
     for (int b = 0; b < steps && e == cudaSuccess; ++b) {
         const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, count);
         e = gf2_apply(ctx->device, (int)ctx->param_set, q + b, rings, hi - lo, iota, iota + lo, scratch,
-                      ctx->sm_count, s, &st);
+                      ctx->sm_count, s, &st, true);
     }
     if (e == cudaSuccess) {
         substream_scatter_kernel<<<count, 128, 0, s>>>(ctx->st, first, count, rings, d_w0, q,

@@ -34,9 +34,12 @@ size_t gf2_apply_scratch(int device, uint32_t n);
 // the tensor cores when gf2_use_tc(device, n) and scratch (gf2_apply_scratch
 // bytes) is given, else with the table kernel.  Asynchronous on s, except
 // that a power's first use builds it.  After synchronising, a caller that
-// may have used the tensor cores checks gf2_tc_take_failure().
+// may have used the tensor cores checks gf2_tc_take_failure().  The table
+// kernel XORs into the destinations, so it zeroes them first unless the
+// caller says they are zero already (dst_zeroed).
 cudaError_t gf2_apply(int device, int family, int k, uint32_t* rings, uint32_t n, const uint32_t* d_src,
-                      const uint32_t* d_dst, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st);
+                      const uint32_t* d_dst, uint8_t* scratch, int sm_count, cudaStream_t s, xg_status* st,
+                      bool dst_zeroed = false);
 
 // Advance n states by `words` positions: M^words applied to rings[0, n),
 // with rings[n, 2n) as the second buffer (*result_hi: the result ended there)

@@ -146,13 +146,15 @@ xg_status generate_cut(xg_w64_ctx* c, int kind, uint32_t first, uint32_t nstream
                        reinterpret_cast<uint32_t*>(scratch + off_pend), reinterpret_cast<uint64_t*>(scratch + off_pos)};
     cudaError_t e = cudaSuccess;
     if (!h.empty()) e = cudaMemcpyAsync(lists, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
-    // piece 0 of each stream: the stream's own ring (gathered one stream at a time)
+    // every ring zeroed once (the doubling steps XOR into the pieces m > 0),
+    // then piece 0 of each stream: the stream's own ring (one stream at a time)
+    if (e == cudaSuccess) e = cudaMemsetAsync(rings, 0, off_win, s);
     for (uint32_t i = 0; i < nstreams && e == cudaSuccess; ++i)
         e = xg64::launch_gather_rings(c->st, first + i, 1, rings + (size_t)i * K * xg64::kR, s);
     uint8_t* tc_scratch = tc_bytes ? reinterpret_cast<uint8_t*>(scratch + off_tc) : nullptr;
     for (int b = 0; b < steps && e == cudaSuccess; ++b)
         e = xg::gf2_apply(c->device, xg::kJumpSetW64, q + b, rings32, cnt[b], lists + src_off[b], lists + dst_off[b],
-                          tc_scratch, c->sm_count, s, &st);
+                          tc_scratch, c->sm_count, s, &st, true);
     const uint64_t omega = c->weyl_on ? xg64::kOmega : 0;
     if (e == cudaSuccess) e = xg64::launch_init_pieces(c->st, first, nstreams, K, L, rings, pieces, omega, s);
     xg_status gst = XG_OK;
@@ -477,10 +479,13 @@ xg_status xg_w64_seed_substreams(xg_w64_ctx* c, uint32_t first, uint32_t count, 
     e = xg::launch_jump_index(ids, count, 0u, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_w0, c->st.weyl + first, 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = xg64::launch_gather_rings(c->st, first, 1, rings, s);
+    // the destinations 1 .. count - 1, zeroed once for all the steps
+    if (e == cudaSuccess && count > 1)
+        e = cudaMemsetAsync(rings + xg64::kR, 0, (size_t)(count - 1) * xg64::kR * 8, s);
     for (int b = 0; b < steps && e == cudaSuccess; ++b) {
         const uint32_t lo = 1u << b, hi = (uint32_t)std::min<uint64_t>((uint64_t)lo << 1, count);
         e = xg::gf2_apply(c->device, xg::kJumpSetW64, q + b, rings32, hi - lo, iota, iota + lo, tc_scratch,
-                          c->sm_count, s, &st);
+                          c->sm_count, s, &st, true);
     }
     if (e == cudaSuccess)
         e = xg64::launch_substream_scatter(c->st, first, count, rings, d_w0, q, c->weyl_on ? xg64::kOmega : 0, s);
