@@ -996,9 +996,14 @@ def end_to_end(st, stream, torch, L, args, dist=None, ws=1):
     k = max(1, min(args.steps, 10))
     if dist:
         dist.barrier()
+    # each call returns once its outputs are in host memory, so a step's
+    # time is its wall time; the figure is the whole timed region's
+    per_step = []
     t0 = time.perf_counter()
     for _ in range(k):
+        ts = time.perf_counter()
         step()
+        per_step.append(time.perf_counter() - ts)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     dt = max_over_ranks(dt * 1e3, dist, "cuda") / 1e3
@@ -1017,12 +1022,15 @@ def end_to_end(st, stream, torch, L, args, dist=None, ws=1):
     del src
     box_gbs = STREAMS * N_PER * 4 / best / 1e9
     e2e_gbs = STREAMS * N_PER * 8 * k / dt / 1e9 if ws == 1 else None
+    med_gbs = STREAMS * N_PER * 8 / statistics.median(per_step) / 1e9
     return {"value": rns, "unit": UNIT, "h2d_bytes_per_step": 0,
             "d2h_bytes_per_step": STREAMS * N_PER * 8 * ws, "steps": k,
-            "d2h_gbs": e2e_gbs, "box_d2h_copy_gbs": box_gbs,
+            "d2h_gbs": e2e_gbs, "median_step_d2h_gbs": med_gbs, "box_d2h_copy_gbs": box_gbs,
             "frac_of_box_d2h": (e2e_gbs / box_gbs) if e2e_gbs else None,
             "note": "host buffers are pinned; no inputs cross per step (state resident); "
-                    "box_d2h_copy_gbs = a plain 4 GiB device-to-host copy into the same buffer"}
+                    "box_d2h_copy_gbs = a plain 4 GiB device-to-host copy into the same buffer (best "
+                    "of 3); single calls on this shared host are sometimes several times slower "
+                    "than the rest, which the median step shows beside the whole-region figure"}
 
 
 def profile_kernel(args):
