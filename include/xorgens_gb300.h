@@ -249,7 +249,7 @@ xg_status xg_autotune_batch(xg_ctx* ctx, const xg_item* items, uint32_t n_items,
  * warps generate at once; each piece starts from the stream's state jumped
  * ahead by its offset (see xg_jump), so the output is exactly that of the
  * uncut call.  piece_words: 0 = automatic (about the batch's words per
- * resident warp, between 2^16 and 2^22), 1 = never cut, else a power of two
+ * resident warp, between 2^15 and 2^22), 1 = never cut, else a power of two
  * >= 64. */
 xg_status xg_set_batch_split(xg_ctx* ctx, uint64_t piece_words);
 

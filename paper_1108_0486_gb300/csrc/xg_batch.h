@@ -69,7 +69,9 @@ public:
     // the price of jump-ahead work, about 2.2e4 words' worth per piece).
     xg_status launch(xg_ctx* c, const HostItem* items, uint32_t n, cudaStream_t s,
                      uint32_t* units_per_item = nullptr, uint64_t min_piece = kMinPiece);
-    static constexpr uint64_t kMinPiece = uint64_t(1) << 16;
+    // 2^15: on an idle GPU the serving p99 is lowest there (2^14 and 2^13 add
+    // more jump-ahead than they save; 2^16 leaves longer chains)
+    static constexpr uint64_t kMinPiece = uint64_t(1) << 15;
     // Preallocate the jump prologue's buffers for up to `pieces` pieces (so
     // that a later launch does not allocate).
     xg_status reserve_jump(uint32_t pieces, uint32_t pairs);

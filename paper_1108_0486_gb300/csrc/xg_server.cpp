@@ -330,7 +330,7 @@ public:
             // room for requests cut into pieces, so the first ones do not allocate
             if (xg_status s = l.launcher->reserve_jump(2048, 4096)) return fail(s, "server: jump buffers");
         }
-        // the jump powers a cut request can need (pieces of 2^16..2^22 words,
+        // the jump powers a cut request can need (pieces of 2^15..2^22 words,
         // calls up to 2^32 words), built now rather than on the first request
         for (int k = 0; k <= 32; ++k) {
             xg_status st = XG_OK;
@@ -657,11 +657,14 @@ private:
     // GPU already has in flight: cutting shortens one call's critical path
     // but costs jump-ahead work (about 2.2e4 words' worth per piece), which
     // only pays while the GPU would otherwise idle.  B is about 1.5 ms of
-    // work: 2^18 words for each of 32 warps per SM.
+    // work: 2^18 words for each of 32 warps per SM.  2^15 only while the GPU
+    // is nearly idle (below B/32): at about a third of the GPU's rate the
+    // extra jump-ahead of 2^15-word pieces tripled the p99 against 2^16.
     uint64_t min_piece_for_backlog() const
     {
         const uint64_t B = (uint64_t)c_->sm_count * 32 * (uint64_t(1) << 18);
-        if (inflight_words_ < B / 8) return BatchLauncher::kMinPiece;
+        if (inflight_words_ < B / 32) return BatchLauncher::kMinPiece;
+        if (inflight_words_ < B / 8) return uint64_t(1) << 16;
         if (inflight_words_ < B) return uint64_t(1) << 18;
         return uint64_t(1) << 21;
     }
