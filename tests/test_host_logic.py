@@ -53,3 +53,28 @@ def test_bench_clock_record_rules():
     assert bench._throttled(dict(ok, reasons=["hw_thermal_slowdown"]))
     assert bench._throttled(dict(ok, sm_mhz=1500.0))
     assert not bench._throttled({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the CPU oracle (the reference arm) and
+    prints one JSON line with the contract's keys, its metric and config
+    those of the GPU arm, a cpu_baseline describing the run and an e2e
+    object with no bytes crossing."""
+    import json
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "3"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["warmup"] >= 3
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["unit"] == "RN/s"
+    assert "workload" in line["config"]
+    base = line["cpu_baseline"]
+    assert base["kind"] == "oracle" and base["cores"] >= 1 and base["value"] == line["value"] and base["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
